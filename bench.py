@@ -1,0 +1,343 @@
+"""Throughput benchmark: batched linearised backward-Euler steps of thin plates/shells on GB300.
+
+Workload (default ``batch256``): 256 independent instances, grid side log-uniform in [8, 128] cells, half
+plates (1 m square, one edge clamped) and half 90-degree cylinder panels (radius U(0.3, 2), both straight
+edges clamped), bending model uniform over the six, E log-uniform in [1e5, 1e8] Pa, nu U(0.2, 0.45),
+thickness 1e-3 m, density 1000 kg/m^3, gravity, dt = 1e-2 s. All instances are stepped together: per step
+one force launch and one persistent solve launch (graph-replayed when not profiling).
+
+Printed line (one JSON object, rank 0):
+  value      vertex-steps/s of the batched FP32 + FP64-refinement path (device-timed, inputs resident),
+  fp64       the plain FP64 path on the same batch, same steps,
+  accuracy   max over instances of |x_fp32r - x_fp64| / |x_fp64 - X| after the same steps (the FP64 path
+             matches the FP64 oracle to 1e-10 in the parity tests),
+  latency    p50 / p99 per-step device time of the batch,
+  e2e        the same metric through the public C ABI with host buffers (per step: host->device state of
+             every instance from pinned memory, the step, device->host state),
+  roofline   the solve kernel (dominant): algorithmic bytes per launch / mean launch time vs measured HBM,
+  cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload.
+
+``--impl reference`` times the FP64 CPU oracle alone on the same workload (bounded sample per step).
+Multi-GPU (torchrun): each rank runs its own batch of the same size (different seeds), no collective on the
+data path; value = all ranks' vertex-steps / the slowest rank's time ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertex-steps/s, batched FP32+refine vs plain FP64 at ≤1e-6 rel err; p50/p99"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch256")
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name, seed, rank):
+    import shellgen as sg
+    if name == "batch256":
+        return sg.mixed_batch(256, seed=seed + 1000 * rank, steps=500), "256 mixed instances, side 8-128 cells"
+    if name.startswith("batch"):
+        n = int(name[5:])
+        return sg.mixed_batch(n, seed=seed + 1000 * rank, steps=500), f"{n} mixed instances"
+    if name == "cyl128":
+        return [sg.cylinder_panel(128, "SS")], "cylinder panel 128x128 cells, SS"
+    if name == "jitter512":
+        return [sg.jittered_plate(512)], "jittered plate 512^2 vertices, SP"
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------ bytes model
+def algorithmic_bytes(info, stats, steps):
+    """Compulsory DRAM bytes of the solve kernel (FP32 + refinement) for ``steps`` steps of one instance.
+
+    Per step: right-hand side 16 B per contribution slot (FP32 force + its index) + 141 B per row, commit 96 B
+    per row. Per refinement round: FP64 matrix 12 B per nonzero + 216 B per row (FP64 residual, vector
+    gather, inner-solve set-up, correction accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero
+    + 168 B per row (update of r, p, s, x and the gathered vector; w = A u; one gather per row).
+    Structural nonzeros are used (padding of the SELL layout is overhead, not algorithmic).
+    """
+    V, nnz, slots = info["n_verts"], info["nnz"], info["n_slots"]
+    per_step = 16.0 * slots + (141.0 + 96.0) * V
+    per_round = 12.0 * nnz + 216.0 * V
+    per_iter = 8.0 * nnz + 168.0 * V
+    return steps * per_step + stats["total_refine_rounds"] * per_round + stats["total_pcg_iterations"] * per_iter
+
+
+# ------------------------------------------------------------------------------------------ oracle timing
+def time_oracle(scs, budget_s, max_steps=5):
+    """FP64 CPU oracle on a bounded sample: instances in order, a few steps each, until ~budget_s of stepping."""
+    from oracle import system as osys
+    done_vs, t_step, n_inst, steps_each = 0, 0.0, 0, max_steps
+    for sc in scs:
+        m = osys.from_scenario(sc)
+        t0 = time.perf_counter()
+        osys.step(m, sc.x0, sc.v0, steps_each)
+        t_step += time.perf_counter() - t0
+        done_vs += sc.n_verts * steps_each
+        n_inst += 1
+        if t_step >= budget_s:
+            break
+    return done_vs / t_step, f"first {n_inst} instances of the workload, {steps_each} steps each, step time only", t_step
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        # the FP64 CPU oracle on this arm's workload and metric; rank 0 only
+        if rank != 0:
+            return
+        scs, desc = workload(args.workload, args.seed, 0)
+        per_step_budget = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        vals = []
+        for _ in range(args.warmup + args.steps):
+            v, sample, _ = time_oracle(scs, per_step_budget, max_steps=1)
+            vals.append(v)
+        vals = vals[args.warmup:]
+        value = float(np.median(vals))
+        emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "vertex-steps/s", "n_gpus": 1,
+              "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+              "data": "synthetic", "config": {"workload": args.workload, "description": desc},
+              "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                               "unit": "vertex-steps/s"},
+              "e2e": {"value": value, "unit": "vertex-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+        return
+
+    import torch
+    import paper_2502_10872_gb300 as gb
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    gb.load_library()
+    scs, desc = workload(args.workload, args.seed, rank)
+    V_total = sum(sc.n_verts for sc in scs)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def make_batch(precision):
+        hs = [gb.create_from_scenario(sc, precision=precision) for sc in scs]
+        b = gb.shell_batch_create(1 << 50)
+        for h in hs:
+            gb.shell_batch_admit(b, h)
+        return b, hs
+
+    def timed(b, K, W, profile):
+        gb.shell_batch_step(b, W)
+        barrier()
+        gb.shell_batch_set_profiling(b, profile)
+        t0 = time.perf_counter()
+        rc, stats = gb.shell_batch_step(b, K)
+        barrier()
+        wall = time.perf_counter() - t0
+        gb.shell_batch_set_profiling(b, False)
+        times = gb.shell_batch_step_times(b, K)
+        kern = gb.shell_batch_kernel_times(b) if profile else None
+        return stats, times, kern, wall
+
+    K, W = args.steps, max(3, args.warmup)
+    # ---- FP32 + refinement (headline)
+    b32, h32 = make_batch("fp32_refine")
+    with Clocks(dev) as clk:
+        stats32, times32, kern32, wall32 = timed(b32, K, W, profile=True)
+    dev_s = float(np.sum(times32)) / 1000.0
+    t_rank = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
+    t_max = float(t_rank.item())
+    value = V_total * K * world / t_max
+    p50, p99 = float(np.percentile(times32, 50)), float(np.percentile(times32, 99))
+
+    # ---- roofline of the solve kernel
+    infos = [gb.shell_info(h) for h in h32]
+    algo = sum(algorithmic_bytes(infos[k], stats32[k], K) for k in range(len(h32)))
+    solve_s = kern32[1] / 1000.0
+    achieved = algo / K / (solve_s / K) / 1e9
+    peak, peak_kind = load_peaks()
+    n_launch = K * 2   # per step: one FP32 force launch over all instances, one persistent solve launch
+
+    # ---- plain FP64 on the same batch, same steps
+    fp64 = None
+    acc = None
+    if not args.no_fp64:
+        b64, h64 = make_batch("fp64")
+        stats64, times64, _, _ = timed(b64, K, W, profile=False)
+        fp64_value = V_total * K / (float(np.sum(times64)) / 1000.0)
+        worst = 0.0
+        for k, sc in enumerate(scs):
+            xa, _ = gb.shell_get_state(h32[k])
+            xb, _ = gb.shell_get_state(h64[k])
+            ref = np.linalg.norm(xb - sc.rest)
+            worst = max(worst, np.linalg.norm(xa - xb) / max(ref, 1e-300))
+        fp64 = {"value": fp64_value, "unit": "vertex-steps/s", "p50_ms": float(np.percentile(times64, 50)),
+                "p99_ms": float(np.percentile(times64, 99)),
+                "pcg_iterations_per_step": float(np.mean([s["total_pcg_iterations"] for s in stats64.values()]) / K)}
+        acc = {"max_rel_x_fp32r_vs_fp64": worst, "steps": W + K}
+        gb.shell_batch_destroy(b64)
+        del h64
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Ke = min(K, 10)
+        pin_x = [torch.empty((sc.n_verts, 3), dtype=torch.float64, pin_memory=True).numpy() for sc in scs]
+        pin_v = [torch.empty((sc.n_verts, 3), dtype=torch.float64, pin_memory=True).numpy() for sc in scs]
+        for k, h in enumerate(h32):
+            x, v = gb.shell_get_state(h)
+            pin_x[k][:] = x
+            pin_v[k][:] = v
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            for k, h in enumerate(h32):
+                gb.shell_set_state(h, pin_x[k], pin_v[k])
+            gb.shell_batch_step(b32, 1)
+            for k, h in enumerate(h32):
+                x, v = gb.shell_get_state(h)
+                pin_x[k][:] = x
+                pin_v[k][:] = v
+        barrier()
+        te = time.perf_counter() - t0
+        e2e = {"value": V_total * Ke * world / te, "unit": "vertex-steps/s", "steps": Ke,
+               "h2d_bytes_per_step": 48 * V_total, "d2h_bytes_per_step": 48 * V_total}
+
+    cpu = None
+    if rank == 0:
+        v, sample, secs = time_oracle(scs, args.cpu_seconds)
+        cpu = {"value": v, "unit": "vertex-steps/s", "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 2)}
+
+    iters = [s["total_pcg_iterations"] / K for s in stats32.values()]
+    rounds = [s["total_refine_rounds"] / K for s in stats32.values()]
+    line = {
+        "metric": METRIC, "value": value, "unit": "vertex-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "instances": len(scs), "vertices": V_total,
+                   "precision": "fp32_refine", "refine_rtol": 1e-10, "pcg_rtol_inner": 1e-4,
+                   "l2": "inputs larger than L2 (batch working set > 129 MB)", "seed": args.seed,
+                   "parallelism": f"instances per rank, {world} rank(s)"},
+        "latency_ms": {"p50": p50, "p99": p99},
+        "fp64": fp64, "accuracy": acc,
+        "solver": {"mean_inner_iterations_per_step": float(np.mean(iters)),
+                   "max_inner_iterations_per_step": float(np.max(iters)),
+                   "mean_refine_rounds_per_step": float(np.mean(rounds))},
+        "roofline": {"kernel": "k_solve", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": algo / K, "mean_launch_ms": kern32[1] / K,
+                     "force_kernel_ms_per_step": kern32[0] / K},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),
+        "wall_s_timed": wall32,
+    }
+    if rank == 0:
+        emit(line)
+    gb.shell_batch_destroy(b32)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

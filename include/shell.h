@@ -1,0 +1,221 @@
+/*
+ * shell.h -- C ABI of the GB300 (sm_103a) corotational hinge-based thin plate / shell library.
+ *
+ * The library advances triangle-mesh thin plates and shells in time under the six corotational bending
+ * models of "Corotational Hinge-based Thin Plates/Shells" (Liang, arXiv 2502.10872): edge-based hinge
+ * (EP/ES, Section 4.3), FVM hinge (FP/FS, Section 4.4) and smoothed hinge (SP/SS, Section 4.5), each as a
+ * plate (rest-flat) and a shell (rest-curved) variant. One step is the linearised backward-Euler step of
+ * the elastodynamic incremental potential (Section 5, Eq. 62-63) with the constant bending Hessian the
+ * models share (Eq. 21, Eq. 41, Eq. 53):
+ *
+ *     (M + dt^2 K) v' = M v + dt (f(x) + f_ext),   x' = x + dt v',
+ *
+ * f = -grad(Psi_m + Psi_b) evaluated exactly at x (bending: Eq. 22, Eq. 25-26, Eq. 44-45, Eq. 56-57),
+ * K = K_b + K_m constant and assembled once on the device at shell_create, M the lumped mass. The membrane
+ * is the corotated linear constant-strain triangle (the paper adopts a constant-strain triangle membrane,
+ * Section 3); its constant matrix block is 2 (mu + lam) A t grad(phi_a).grad(phi_b) per triangle, with
+ * mu = E / (2 (1 + nu)) and lam = E nu / (1 - nu^2). The linear system is solved by Jacobi-preconditioned
+ * conjugate gradients on the GPU, either in FP64 or in FP32 with FP64 iterative refinement of the residual.
+ *
+ * Every step of the path runs in CUDA kernels: rest-state precompute (FP64), matrix assembly (FP64),
+ * per-stencil forces, right-hand side, PCG, state update. There is no CPU fallback: without a usable
+ * CUDA device every entry point that needs one returns SHELL_ERR_CUDA or SHELL_ERR_NO_DEVICE.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SHELL_OK (0) on success, a negative SHELL_ERR_* code otherwise; shell_strerror()
+ *     gives a message. On failure no output is written unless stated otherwise.
+ *   - Host arrays passed in are copied; the caller keeps ownership and may free them after the call.
+ *   - Output host buffers are allocated by the caller with the stated size.
+ *   - Calls on one handle (or batch) must be externally serialised. Device work runs on the stream given
+ *     in shell_options.cuda_stream (NULL = the legacy default stream); calls that return host data
+ *     synchronise that stream.
+ *   - Arrays of 3-vectors are row-major [n][3] (x, y, z interleaved) on the host.
+ */
+#ifndef SHELL_H_
+#define SHELL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------------------------ codes */
+#define SHELL_OK 0
+#define SHELL_ERR_INVALID_ARG -1      /* NULL pointer, size out of range, bad enum, non-planar plate rest */
+#define SHELL_ERR_NON_MANIFOLD -2     /* an edge is shared by more than two triangles */
+#define SHELL_ERR_BAD_ORIENTATION -3  /* neighbouring triangles are not consistently oriented */
+#define SHELL_ERR_DEGENERATE -4       /* a rest triangle or stencil height is (numerically) zero */
+#define SHELL_ERR_SINGULAR_OPERATOR -5 /* L_p C_p of a smoothed hinge stencil is singular (Section 4.5) */
+#define SHELL_ERR_OOM -6              /* device allocation failed */
+#define SHELL_ERR_BUDGET -7           /* a batch's memory budget cannot hold the instance */
+#define SHELL_ERR_NOT_CONVERGED -8    /* PCG / refinement hit its iteration cap; the step is not committed */
+#define SHELL_ERR_NONFINITE -9        /* NaN or Inf met in the step; the step is not committed */
+#define SHELL_ERR_TIMEOUT -10         /* a bounded device-side wait gave up; the launch was abandoned */
+#define SHELL_ERR_CUDA -11            /* a CUDA runtime call failed */
+#define SHELL_ERR_NO_DEVICE -12       /* no CUDA device of compute capability 10.3 is available */
+#define SHELL_ERR_BUSY -13            /* the handle belongs to a batch and must be stepped through it */
+
+/* ------------------------------------------------------------------------------------------ enums */
+/* Bending model (Section 4.2): E/F/S = edge-based / FVM / smoothed hinge, P/S = plate / shell. */
+typedef enum shell_model {
+  SHELL_EP = 0,
+  SHELL_ES = 1,
+  SHELL_FP = 2,
+  SHELL_FS = 3,
+  SHELL_SP = 4,
+  SHELL_SS = 5
+} shell_model;
+
+/* Arithmetic of the per-step force and linear solve. SHELL_FP64: everything in FP64.
+ * SHELL_FP32_REFINE: forces and PCG in FP32, the right-hand side, the solution and the residual of an
+ * outer iterative refinement in FP64 (positions and velocities are always held in FP64). */
+typedef enum shell_precision { SHELL_FP64 = 0, SHELL_FP32_REFINE = 1 } shell_precision;
+
+/* ------------------------------------------------------------------------------------------ inputs */
+typedef struct shell_mesh {
+  int32_t n_verts;          /* V >= 3 */
+  int32_t n_tris;           /* T >= 1 */
+  const int32_t *tris;      /* [T][3] vertex indices, consistently oriented, manifold */
+  const double *rest_xyz;   /* [V][3] rest shape X (planar within 1e-9 * size for plate models) */
+  const double *init_xyz;   /* [V][3] initial positions x, or NULL for x = X */
+  const double *init_vel;   /* [V][3] initial velocities, or NULL for zero */
+} shell_mesh;
+
+typedef struct shell_material {
+  double E;          /* Young's modulus > 0 */
+  double nu;         /* Poisson's ratio in [0, 0.5) */
+  double thickness;  /* t > 0 (bending rigidity k_b = E t^3 / (12 (1 - nu^2)), Section 4.3) */
+  double density;    /* rho > 0 (lumped mass m_i = sum rho t A / 3 over incident triangles) */
+} shell_material;
+
+/* Boundary conditions (Section 4.3 "Boundary conditions", Eq. 30-31 and Eq. 58-61).
+ * Boundary edges not listed as clamped are free (no edge stencil; the virtual node of a triangle
+ * stencil is folded with w_L' = w_M + w_N - w_L). A clamped edge folds w_L' = w_L, measures transverse
+ * displacement along the fixed rest normal of its stencil, and pins both end vertices. Pinned vertices
+ * keep their position (zero velocity). Simply supported = free edges + pinned vertices. */
+typedef struct shell_bc {
+  const uint8_t *pinned;          /* [V] nonzero = fixed, or NULL */
+  int32_t n_clamped;              /* number of clamped boundary edges */
+  const int32_t *clamped_edges;   /* [n_clamped][2] vertex pairs of boundary edges */
+  double gravity[3];              /* body acceleration; f_ext += m_i * gravity */
+  int32_t n_loads;                /* point loads */
+  const int32_t *load_vtx;        /* [n_loads] */
+  const double *load_f;           /* [n_loads][3] newtons */
+} shell_bc;
+
+/* Device memory hooks: if alloc is NULL the library uses cudaMallocAsync / cudaFreeAsync on the handle's
+ * stream. Hooks must return 256-byte aligned device memory (or NULL on failure). */
+typedef void *(*shell_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
+typedef void (*shell_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *user);
+
+typedef struct shell_options {
+  double dt;               /* time step > 0 */
+  int32_t precision;       /* shell_precision */
+  double pcg_rtol;         /* stop when ||r|| <= pcg_rtol ||b|| (FP64); inner relative tolerance (FP32) */
+  double refine_rtol;      /* FP32_REFINE: stop when the FP64 residual ||b - A v|| <= refine_rtol ||b|| */
+  int32_t pcg_max_it;      /* iteration cap per solve (per inner solve in FP32_REFINE) */
+  int32_t refine_max;      /* FP32_REFINE: cap on refinement rounds */
+  void *cuda_stream;       /* cudaStream_t, or NULL */
+  shell_alloc_fn alloc;    /* optional device allocator */
+  shell_free_fn free;
+  void *alloc_user;
+} shell_options;
+
+/* Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
+ * FP64 PCG, 1e-4 for the inner FP32 PCG, 1e-10 for the refinement), pcg_max_it 20000, refine_max 20. */
+void shell_default_options(shell_options *opt);
+
+/* Statistics of the last shell_step / shell_batch_step call for one instance. */
+typedef struct shell_step_stats {
+  int32_t steps_done;          /* steps committed by this call */
+  int32_t pcg_iterations;      /* PCG iterations of the last committed step (summed over rounds) */
+  int32_t refine_rounds;       /* refinement rounds of the last committed step (0 in FP64) */
+  int32_t status;              /* SHELL_OK or the error that stopped this instance */
+  int64_t total_pcg_iterations;/* summed over the call's steps */
+  double rel_residual;         /* ||b - A v'|| / ||b|| of the last committed step (recursive in FP64) */
+  int64_t total_refine_rounds; /* summed over the call's steps */
+} shell_step_stats;
+
+/* ------------------------------------------------------------------------------------------ handle */
+typedef struct shell_handle shell_handle;
+
+/* Build one simulation (Section 4 rest-state precompute and the constant matrix, assembled once).
+ * Validates the mesh (manifold, consistent orientation, non-degenerate), builds the stencils on the host,
+ * uploads them and runs the FP64 precompute and assembly kernels. *out receives an owning handle.
+ * Errors: INVALID_ARG, NON_MANIFOLD, BAD_ORIENTATION, DEGENERATE, SINGULAR_OPERATOR, OOM, CUDA, NO_DEVICE. */
+int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t model, const shell_bc *bc,
+                 const shell_options *opt, shell_handle **out);
+
+/* Advance n_steps >= 0 steps. Each step: per-stencil forces at the current x, right-hand side, PCG (and
+ * refinement), x += dt v'. A step that fails (NOT_CONVERGED, NONFINITE, TIMEOUT) is not committed and
+ * ends the call; the steps before it are committed. stats may be NULL. */
+int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
+
+/* Energies at the current state, FP64: out[0] membrane, out[1] bending, out[2] kinetic 1/2 v^T M v,
+ * out[3] external potential -sum f_ext . (x - X). */
+int shell_energy(shell_handle *h, double out[4]);
+
+/* Elastic forces -grad(Psi_m + Psi_b) at the current x in FP64, written to out_xyz [V][3] (host). */
+int shell_forces(shell_handle *h, double *out_xyz);
+
+/* Apply the constant step matrix A = M + dt^2 (K_b + K_m) (identity rows / columns at pinned vertices; the
+ * matrix is the scalar matrix (x) I_3) to in_xyz [V][3] in FP64: out_xyz = A in_xyz (host buffers). */
+int shell_apply_matrix(shell_handle *h, const double *in_xyz, double *out_xyz);
+
+/* Copy the state to / from host buffers [V][3] (either pointer may be NULL to skip it). */
+int shell_get_state(shell_handle *h, double *x, double *v);
+int shell_set_state(shell_handle *h, const double *x, const double *v);
+
+/* Device-pointer variants: [V][3] row-major FP64 device buffers, stream ordered, no synchronisation. */
+int shell_get_state_device(shell_handle *h, double *d_x, double *d_v);
+int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v);
+
+/* Sizes: out[0] vertices, out[1] triangles, out[2] bending stencils, out[3] bytes of device memory the handle
+ * holds, out[4] structural nonzeros of the scalar matrix, out[5] stored (SELL-padded) nonzeros, out[6]
+ * force contribution slots. */
+int shell_info(shell_handle *h, int64_t out[7]);
+
+int shell_destroy(shell_handle *h);
+const char *shell_strerror(int code);
+
+/* Host-only mesh check (needs no GPU): builds the stencils and the matrix structure shell_create would
+ * build and checks every index they hold. out[0] interior edge stencils (edge hinge models), out[1]
+ * clamped edge stencils, out[2] triangle stencils with a virtual neighbour, out[3] structural nonzeros of
+ * the scalar matrix, out[4] stored (SELL-padded) nonzeros, out[5] force contribution slots, out[6] local
+ * matrix entries assembled, out[7] 0 if every index is in range (else the number of bad indices).
+ * Errors: INVALID_ARG, NON_MANIFOLD, BAD_ORIENTATION. */
+int shell_topology_summary(int32_t n_verts, int32_t n_tris, const int32_t *tris, int32_t n_clamped,
+                           const int32_t *clamped_edges, int32_t model, int64_t out[8]);
+
+/* ------------------------------------------------------------------------------------------ batch */
+/* A batch steps many independent handles together: one force launch and one persistent solve launch per
+ * step for all resident instances, replayed from a CUDA graph. Instances are admitted while the batch's
+ * device-memory budget (bytes of the admitted handles) allows; each instance's result does not depend on
+ * the other instances in the batch. A handle admitted to a batch cannot be stepped alone until retired. */
+typedef struct shell_batch shell_batch;
+
+int shell_batch_create(const shell_options *opt, size_t budget_bytes, shell_batch **out);
+/* Admit a handle; *slot receives its slot id. Errors: BUDGET if it does not fit, BUSY if already in one. */
+int shell_batch_admit(shell_batch *b, shell_handle *h, int32_t *slot);
+int shell_batch_retire(shell_batch *b, int32_t slot);
+/* Step every resident instance n_steps times. stats: NULL or an array indexed by slot with room for
+ * shell_batch_capacity() entries. Instances that fail stop stepping; the others continue. Returns the
+ * first error met, or SHELL_OK. */
+int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats);
+int shell_batch_capacity(shell_batch *b);
+/* Device time of the last shell_batch_step, per step, in milliseconds: out[k] for k < n (n <= steps). */
+int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
+/* Kernel timing of later shell_batch_step calls: with on != 0 every step is launched directly (not from
+ * the graph) with CUDA events around the force launches and the solve launch. shell_batch_kernel_times
+ * then gives out_ms[0] = summed force-kernel time and out_ms[1] = summed solve-kernel time of the last
+ * call, in milliseconds. */
+int shell_batch_set_profiling(shell_batch *b, int32_t on);
+int shell_batch_kernel_times(shell_batch *b, double out_ms[2]);
+int shell_batch_destroy(shell_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHELL_H_ */

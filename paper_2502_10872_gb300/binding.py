@@ -1,0 +1,435 @@
+"""ctypes binding of the C ABI in ``include/shell.h`` (argument marshalling only).
+
+Every function here forwards to the CUDA library ``libshells.so`` built in-tree by
+``paper_2502_10872_gb300._build``; there is no CPU implementation behind it. If the library is missing the
+import of a function raises :class:`LibraryNotBuilt`; without a GB300 the calls return
+``SHELL_ERR_NO_DEVICE`` (raised as :class:`ShellError`).
+
+Device memory is allocated through PyTorch's caching allocator when PyTorch with CUDA is available (the
+library's allocator hooks), and work runs on PyTorch's current stream unless a stream is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshells.so")
+
+SHELL_OK = 0
+ERRORS = {
+    -1: "SHELL_ERR_INVALID_ARG", -2: "SHELL_ERR_NON_MANIFOLD", -3: "SHELL_ERR_BAD_ORIENTATION",
+    -4: "SHELL_ERR_DEGENERATE", -5: "SHELL_ERR_SINGULAR_OPERATOR", -6: "SHELL_ERR_OOM", -7: "SHELL_ERR_BUDGET",
+    -8: "SHELL_ERR_NOT_CONVERGED", -9: "SHELL_ERR_NONFINITE", -10: "SHELL_ERR_TIMEOUT", -11: "SHELL_ERR_CUDA",
+    -12: "SHELL_ERR_NO_DEVICE", -13: "SHELL_ERR_BUSY",
+}
+for _c, _n in ERRORS.items():
+    globals()[_n] = _c
+MODELS = {"EP": 0, "ES": 1, "FP": 2, "FS": 3, "SP": 4, "SS": 5}
+PRECISIONS = {"fp64": 0, "fp32_refine": 1}
+
+# symbols declared in include/shell.h
+EXPORTS = (
+    "shell_default_options", "shell_strerror", "shell_create", "shell_step", "shell_energy", "shell_forces",
+    "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
+    "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
+    "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
+    "shell_batch_destroy",
+)
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class ShellError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = f"{ERRORS.get(code, code)}: {_strerror(code)}"
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+# ------------------------------------------------------------------------------------------ structs
+class shell_mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("tris", C.c_void_p), ("rest_xyz", C.c_void_p),
+                ("init_xyz", C.c_void_p), ("init_vel", C.c_void_p)]
+
+
+class shell_material(C.Structure):
+    _fields_ = [("E", C.c_double), ("nu", C.c_double), ("thickness", C.c_double), ("density", C.c_double)]
+
+
+class shell_bc(C.Structure):
+    _fields_ = [("pinned", C.c_void_p), ("n_clamped", C.c_int32), ("clamped_edges", C.c_void_p),
+                ("gravity", C.c_double * 3), ("n_loads", C.c_int32), ("load_vtx", C.c_void_p),
+                ("load_f", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class shell_options(C.Structure):
+    _fields_ = [("dt", C.c_double), ("precision", C.c_int32), ("pcg_rtol", C.c_double),
+                ("refine_rtol", C.c_double), ("pcg_max_it", C.c_int32), ("refine_max", C.c_int32),
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+
+
+class shell_step_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int32), ("pcg_iterations", C.c_int32), ("refine_rounds", C.c_int32),
+                ("status", C.c_int32), ("total_pcg_iterations", C.c_int64), ("rel_residual", C.c_double),
+                ("total_refine_rounds", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# ------------------------------------------------------------------------------------------ loading
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``libshells.so`` (raises :class:`LibraryNotBuilt` if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LibraryNotBuilt(f"{path} not found: run paper_2502_10872_gb300._build.build() (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "shell_default_options": (None, [C.POINTER(shell_options)]),
+        "shell_strerror": (C.c_char_p, [C.c_int]),
+        "shell_create": (C.c_int, [C.POINTER(shell_mesh), C.POINTER(shell_material), C.c_int32, C.POINTER(shell_bc),
+                                   C.POINTER(shell_options), C.POINTER(P)]),
+        "shell_step": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
+        "shell_energy": (C.c_int, [P, P]),
+        "shell_forces": (C.c_int, [P, P]),
+        "shell_apply_matrix": (C.c_int, [P, P, P]),
+        "shell_get_state": (C.c_int, [P, P, P]),
+        "shell_set_state": (C.c_int, [P, P, P]),
+        "shell_get_state_device": (C.c_int, [P, P, P]),
+        "shell_set_state_device": (C.c_int, [P, P, P]),
+        "shell_info": (C.c_int, [P, P]),
+        "shell_destroy": (C.c_int, [P]),
+        "shell_topology_summary": (C.c_int, [C.c_int32, C.c_int32, P, C.c_int32, P, C.c_int32, P]),
+        "shell_batch_create": (C.c_int, [C.POINTER(shell_options), C.c_size_t, C.POINTER(P)]),
+        "shell_batch_admit": (C.c_int, [P, P, C.POINTER(C.c_int32)]),
+        "shell_batch_retire": (C.c_int, [P, C.c_int32]),
+        "shell_batch_step": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
+        "shell_batch_capacity": (C.c_int, [P]),
+        "shell_batch_step_times": (C.c_int, [P, P, C.c_int32]),
+        "shell_batch_set_profiling": (C.c_int, [P, C.c_int32]),
+        "shell_batch_kernel_times": (C.c_int, [P, P]),
+        "shell_batch_destroy": (C.c_int, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _strerror(code: int) -> str:
+    try:
+        return load_library().shell_strerror(code).decode()
+    except LibraryNotBuilt:
+        return ERRORS.get(code, str(code))
+
+
+def _check(code: int, what: str):
+    if code != SHELL_OK:
+        raise ShellError(code, what)
+
+
+# ------------------------------------------------------------------------------------------ allocator
+_torch_hooks = None
+
+
+def _torch_allocator():
+    """(alloc, free) ctypes callbacks into PyTorch's CUDA caching allocator, or None."""
+    global _torch_hooks
+    if _torch_hooks is not None:
+        return _torch_hooks
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+    except Exception:
+        return None
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0)))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        if ptr:
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    _torch_hooks = (ALLOC_FN(_alloc), FREE_FN(_free))
+    return _torch_hooks
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+def make_options(dt=1e-2, precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
+                 stream: Optional[int] = None, use_torch_allocator: bool = True) -> shell_options:
+    lib = load_library()
+    o = shell_options()
+    lib.shell_default_options(C.byref(o))
+    o.dt = float(dt)
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.pcg_rtol = float(pcg_rtol)
+    o.refine_rtol = float(refine_rtol)
+    o.pcg_max_it = int(pcg_max_it)
+    o.refine_max = int(refine_max)
+    o.cuda_stream = _current_stream() if stream is None else int(stream)
+    hooks = _torch_allocator() if use_torch_allocator else None
+    if hooks:
+        o.alloc, o.free = hooks
+    return o
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data
+
+
+def _arr(a, dtype, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+# ------------------------------------------------------------------------------------------ handle API
+class Handle:
+    """Owning wrapper of a ``shell_handle*``."""
+
+    def __init__(self, ptr, n_verts, opts, keep):
+        self.ptr = ptr
+        self.n_verts = n_verts
+        self._opts = opts
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                load_library().shell_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None, init_vel=None, pinned=None,
+                 clamped_edges=None, gravity=(0.0, 0.0, 0.0), load_vtx=None, load_f=None, dt=1e-2,
+                 precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
+                 stream=None, use_torch_allocator=True) -> Handle:
+    """shell_create: rest-state precompute and constant-matrix assembly on the GPU (see include/shell.h)."""
+    lib = load_library()
+    tris = _arr(tris, np.int32, (-1, 3))
+    rest = _arr(rest, np.float64, (-1, 3))
+    V = rest.shape[0]
+    x0 = _arr(init_xyz, np.float64, (V, 3))
+    v0 = _arr(init_vel, np.float64, (V, 3))
+    pin = _arr(pinned, np.uint8, (V,))
+    ce = _arr(clamped_edges, np.int32, (-1, 2)) if clamped_edges is not None else np.zeros((0, 2), np.int32)
+    lv = _arr(load_vtx, np.int32, (-1,)) if load_vtx is not None else np.zeros((0,), np.int32)
+    lf = _arr(load_f, np.float64, (-1, 3)) if load_f is not None else np.zeros((0, 3), np.float64)
+    mesh = shell_mesh(V, tris.shape[0], _ptr(tris), _ptr(rest), _ptr(x0), _ptr(v0))
+    mat = shell_material(E, nu, thickness, density)
+    bc = shell_bc()
+    bc.pinned = _ptr(pin)
+    bc.n_clamped = ce.shape[0]
+    bc.clamped_edges = _ptr(ce) if ce.shape[0] else None
+    bc.gravity = (C.c_double * 3)(*[float(g) for g in gravity])
+    bc.n_loads = lv.shape[0]
+    bc.load_vtx = _ptr(lv) if lv.shape[0] else None
+    bc.load_f = _ptr(lf) if lv.shape[0] else None
+    opts = make_options(dt, precision, pcg_rtol, refine_rtol, pcg_max_it, refine_max, stream, use_torch_allocator)
+    out = C.c_void_p()
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    _check(lib.shell_create(C.byref(mesh), C.byref(mat), m, C.byref(bc), C.byref(opts), C.byref(out)), "shell_create")
+    return Handle(out.value, V, opts, None)
+
+
+def create_from_scenario(sc, precision="fp64", **kw) -> Handle:
+    """shell_create from any object with the fields of a generated scenario (tris, rest, x0, v0, model, E, nu,
+    thickness, density, pinned, clamped_edges, gravity, load_vtx, load_f, dt)."""
+    return shell_create(sc.tris, sc.rest, sc.model, sc.E, sc.nu, sc.thickness, sc.density, init_xyz=sc.x0,
+                        init_vel=sc.v0, pinned=sc.pinned, clamped_edges=sc.clamped_edges, gravity=sc.gravity,
+                        load_vtx=sc.load_vtx, load_f=sc.load_f, dt=sc.dt, precision=precision, **kw)
+
+
+def shell_step(h: Handle, n_steps: int = 1, check: bool = True) -> dict:
+    st = shell_step_stats()
+    rc = load_library().shell_step(h.ptr, int(n_steps), C.byref(st))
+    if check:
+        _check(rc, "shell_step")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def shell_energy(h: Handle) -> np.ndarray:
+    out = np.zeros(4, np.float64)
+    _check(load_library().shell_energy(h.ptr, out.ctypes.data), "shell_energy")
+    return out
+
+
+def shell_forces(h: Handle) -> np.ndarray:
+    out = np.zeros((h.n_verts, 3), np.float64)
+    _check(load_library().shell_forces(h.ptr, out.ctypes.data), "shell_forces")
+    return out
+
+
+def shell_apply_matrix(h: Handle, vec) -> np.ndarray:
+    """out = A vec with the constant step matrix A = M + dt^2 K (FP64, host buffers)."""
+    a = _arr(vec, np.float64, (h.n_verts, 3))
+    out = np.zeros((h.n_verts, 3), np.float64)
+    _check(load_library().shell_apply_matrix(h.ptr, a.ctypes.data, out.ctypes.data), "shell_apply_matrix")
+    return out
+
+
+def shell_get_state(h: Handle):
+    x = np.zeros((h.n_verts, 3), np.float64)
+    v = np.zeros((h.n_verts, 3), np.float64)
+    _check(load_library().shell_get_state(h.ptr, x.ctypes.data, v.ctypes.data), "shell_get_state")
+    return x, v
+
+
+def shell_set_state(h: Handle, x=None, v=None):
+    xa = _arr(x, np.float64, (h.n_verts, 3))
+    va = _arr(v, np.float64, (h.n_verts, 3))
+    _check(load_library().shell_set_state(h.ptr, _ptr(xa), _ptr(va)), "shell_set_state")
+
+
+def shell_get_state_device(h: Handle, x_dev=None, v_dev=None):
+    """Copy the state into caller-owned device buffers ([V][3] float64 torch tensors), stream ordered."""
+    px = None if x_dev is None else x_dev.data_ptr()
+    pv = None if v_dev is None else v_dev.data_ptr()
+    _check(load_library().shell_get_state_device(h.ptr, px, pv), "shell_get_state_device")
+
+
+def shell_set_state_device(h: Handle, x_dev=None, v_dev=None):
+    px = None if x_dev is None else x_dev.data_ptr()
+    pv = None if v_dev is None else v_dev.data_ptr()
+    _check(load_library().shell_set_state_device(h.ptr, px, pv), "shell_set_state_device")
+
+
+def shell_info(h: Handle) -> dict:
+    out = np.zeros(7, np.int64)
+    _check(load_library().shell_info(h.ptr, out.ctypes.data), "shell_info")
+    return {"n_verts": int(out[0]), "n_tris": int(out[1]), "n_stencils": int(out[2]), "device_bytes": int(out[3]),
+            "nnz": int(out[4]), "nnz_stored": int(out[5]), "n_slots": int(out[6])}
+
+
+def shell_destroy(h: Handle):
+    if h.ptr:
+        _check(load_library().shell_destroy(h.ptr), "shell_destroy")
+        h.ptr = None
+
+
+def shell_topology_summary(tris, n_verts, model, clamped_edges=None) -> dict:
+    """Host-only stencil / matrix-structure check (no GPU needed)."""
+    tris = _arr(tris, np.int32, (-1, 3))
+    ce = _arr(clamped_edges, np.int32, (-1, 2)) if clamped_edges is not None else np.zeros((0, 2), np.int32)
+    out = np.zeros(8, np.int64)
+    m = MODELS[model] if isinstance(model, str) else int(model)
+    _check(load_library().shell_topology_summary(int(n_verts), tris.shape[0], tris.ctypes.data, ce.shape[0],
+                                                 ce.ctypes.data if ce.shape[0] else None, m, out.ctypes.data),
+           "shell_topology_summary")
+    keys = ("edge_stencils", "clamped_edge_stencils", "virtual_tri_stencils", "nnz", "nnz_stored", "n_slots",
+            "n_assembled", "bad_indices")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def shell_strerror(code: int) -> str:
+    return _strerror(code)
+
+
+# ------------------------------------------------------------------------------------------ batch API
+class Batch:
+    def __init__(self, ptr, opts):
+        self.ptr = ptr
+        self._opts = opts
+        self.members = {}
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                load_library().shell_batch_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def shell_batch_create(budget_bytes: int, stream=None, use_torch_allocator=True) -> Batch:
+    opts = make_options(stream=stream, use_torch_allocator=use_torch_allocator)
+    out = C.c_void_p()
+    _check(load_library().shell_batch_create(C.byref(opts), int(budget_bytes), C.byref(out)), "shell_batch_create")
+    return Batch(out.value, opts)
+
+
+def shell_batch_admit(b: Batch, h: Handle, check: bool = True) -> int:
+    slot = C.c_int32(-1)
+    rc = load_library().shell_batch_admit(b.ptr, h.ptr, C.byref(slot))
+    if check:
+        _check(rc, "shell_batch_admit")
+    elif rc != SHELL_OK:
+        return rc
+    b.members[slot.value] = h
+    return slot.value
+
+
+def shell_batch_retire(b: Batch, slot: int):
+    _check(load_library().shell_batch_retire(b.ptr, int(slot)), "shell_batch_retire")
+    b.members.pop(slot, None)
+
+
+def shell_batch_step(b: Batch, n_steps: int = 1, check: bool = True):
+    lib = load_library()
+    cap = lib.shell_batch_capacity(b.ptr)
+    stats = (shell_step_stats * max(1, cap))()
+    rc = lib.shell_batch_step(b.ptr, int(n_steps), stats)
+    if check:
+        _check(rc, "shell_batch_step")
+    return rc, {k: stats[k].as_dict() for k in range(cap) if k in b.members}
+
+
+def shell_batch_step_times(b: Batch, n: int) -> np.ndarray:
+    out = np.zeros(max(1, n), np.float32)
+    k = load_library().shell_batch_step_times(b.ptr, out.ctypes.data, int(n))
+    return out[:max(0, k)]
+
+
+def shell_batch_set_profiling(b: Batch, on: bool = True):
+    _check(load_library().shell_batch_set_profiling(b.ptr, 1 if on else 0), "shell_batch_set_profiling")
+
+
+def shell_batch_kernel_times(b: Batch) -> np.ndarray:
+    out = np.zeros(2, np.float64)
+    _check(load_library().shell_batch_kernel_times(b.ptr, out.ctypes.data), "shell_batch_kernel_times")
+    return out
+
+
+def shell_batch_destroy(b: Batch):
+    if b.ptr:
+        _check(load_library().shell_batch_destroy(b.ptr), "shell_batch_destroy")
+        b.ptr = None
+        b.members.clear()

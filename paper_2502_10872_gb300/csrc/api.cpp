@@ -1,0 +1,1066 @@
+// api.cpp -- the C ABI (include/shell.h): handles, batches, device memory, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "host_mesh.h"
+#include "internal.h"
+
+using namespace shl;
+
+namespace {
+
+#define CK(call)                          \
+  do {                                    \
+    cudaError_t e_ = (call);              \
+    if (e_ != cudaSuccess) {              \
+      last_cuda_error() = e_;             \
+      return SHELL_ERR_CUDA;              \
+    }                                     \
+  } while (0)
+
+cudaError_t &last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+int check_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SHELL_ERR_NO_DEVICE;
+  }
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SHELL_ERR_NO_DEVICE;
+  }
+  if (major != 10 || minor != 3) return SHELL_ERR_NO_DEVICE;
+  return SHELL_OK;
+}
+
+// ---------------------------------------------------------------- device memory
+struct Mem {
+  shell_alloc_fn alloc = nullptr;
+  shell_free_fn free = nullptr;
+  void *user = nullptr;
+  cudaStream_t st = nullptr;
+  void *get(size_t bytes) const {
+    if (bytes == 0) bytes = 256;
+    if (alloc) return alloc(bytes, (void *)st, user);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void *p, size_t bytes) const {
+    if (!p) return;
+    if (free)
+      free(p, bytes, (void *)st, user);
+    else
+      cudaFreeAsync(p, st);
+  }
+};
+
+// carve one allocation into 256-byte aligned arrays: first pass sizes, second pass assigns
+struct Carver {
+  char *base = nullptr;
+  size_t off = 0;
+  template <typename T>
+  T *take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+struct shell_batch;
+
+struct shell_handle {
+  int nv = 0, nt = 0, ne = 0, model = 0;
+  shell_material mat{};
+  shell_options opt{};
+  Mem mem;
+  void *block = nullptr;
+  size_t block_bytes = 0;
+  Inst h{};                 // descriptor with device pointers
+  Inst *d_inst = nullptr;   // device copy
+  double *d_stage = nullptr;  // [2][V][3] staging for row-major state transfers
+  double *d_energy = nullptr; // [4]
+  double *d_forces = nullptr; // [V][3]
+  shell_batch *batch = nullptr;  // user batch holding this handle
+  int32_t slot = -1;
+  shell_batch *solo = nullptr;   // private batch used by shell_step
+  std::vector<Tile> tiles;       // force tiles of this instance (inst index filled by the batch)
+  Tile *d_tiles = nullptr;       // the same tiles on the device (inst index 0 = d_inst)
+  double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
+  int64_t nnz = 0, nnz_pad = 0;
+  InstStatus last_status{};
+};
+
+struct shell_batch {
+  shell_options opt{};
+  Mem mem;
+  size_t budget = 0, used = 0;
+  std::vector<shell_handle *> slots;
+  bool dirty = true;
+  bool solo = false;
+  // device tables
+  void *tbl = nullptr;
+  size_t tbl_bytes = 0;
+  Inst *d_insts = nullptr;
+  Tile *d_tiles64 = nullptr, *d_tiles32 = nullptr;
+  int n_tiles64 = 0, n_tiles32 = 0;
+  Sched sched{};
+  int grid = 0;
+  int n_teams = 0;
+  int n_active = 0;
+  InstStatus *d_status_out = nullptr;
+  int32_t *d_abort_out = nullptr;
+  std::vector<int> active;   // slot ids in table order
+  std::vector<cudaEvent_t> events;
+  std::vector<float> step_ms;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_tried = false;
+  bool profiling = false;
+  std::vector<cudaEvent_t> pev;   // 3 per profiled step
+  double kern_ms[2] = {0.0, 0.0};
+};
+
+namespace {
+
+int blocks_per_sm_cached() {
+  static int n = -1;
+  if (n < 0) n = std::max(1, solve_blocks_per_sm());
+  return n;
+}
+int num_sms() {
+  static int n = -1;
+  if (n < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return n;
+}
+
+void destroy_graph(shell_batch *b) {
+  if (b->gexec) {
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  b->graph_tried = false;
+}
+
+// Build the force tile lists and the persistent-solve schedule for the resident instances.
+int rebuild_tables(shell_batch *b) {
+  destroy_graph(b);
+  b->active.clear();
+  for (size_t k = 0; k < b->slots.size(); ++k)
+    if (b->slots[k]) b->active.push_back((int)k);
+  const int n = (int)b->active.size();
+  b->n_active = n;
+  if (n == 0) {
+    b->dirty = false;
+    return SHELL_OK;
+  }
+  std::vector<Inst> insts(n);
+  std::vector<Tile> t64, t32;
+  for (int k = 0; k < n; ++k) {
+    shell_handle *h = b->slots[b->active[k]];
+    insts[k] = h->h;
+    for (Tile t : h->tiles) {
+      t.inst = k;
+      (h->h.precision == SHELL_FP64 ? t64 : t32).push_back(t);
+    }
+  }
+  // ---- schedule: teams of CTAs, each working through a list of instances
+  const int G = num_sms() * blocks_per_sm_cached();
+  std::vector<double> work(n);
+  double total = 0.0;
+  for (int k = 0; k < n; ++k) {
+    shell_handle *h = b->slots[b->active[k]];
+    work[k] = (double)h->nv * std::max(1.0, h->est_iters);
+    total += work[k];
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
+  const double share = total / G;
+  std::vector<int> team_size, team_of(n, -1);
+  std::vector<std::vector<int>> team_inst;
+  int used = 0;
+  // big instances get their own multi-CTA team sized by their share of the work
+  for (int k : order) {
+    const shell_handle *h = b->slots[b->active[k]];
+    int want = (int)std::floor(work[k] / share);
+    want = std::min(want, h->h.n_chunks);
+    if (want < 2) break;
+    int left_small = 0;
+    for (int q = 0; q < n; ++q)
+      if (team_of[q] < 0 && q != k) ++left_small;
+    const int room = G - used - (left_small > 0 ? 1 : 0);
+    want = std::min(want, room);
+    if (want < 2) break;
+    team_of[k] = (int)team_size.size();
+    team_size.push_back(want);
+    team_inst.push_back({k});
+    used += want;
+  }
+  // the rest: single-CTA teams, longest-processing-time first
+  std::vector<int> small;
+  for (int k : order)
+    if (team_of[k] < 0) small.push_back(k);
+  if (!small.empty()) {
+    const int n1 = std::max(1, std::min((int)small.size(), G - used));
+    const int first = (int)team_size.size();
+    std::vector<double> load(n1, 0.0);
+    for (int q = 0; q < n1; ++q) {
+      team_size.push_back(1);
+      team_inst.push_back({});
+    }
+    for (int k : small) {
+      int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[best] += work[k];
+      team_inst[first + best].push_back(k);
+      team_of[k] = first + best;
+    }
+    used += n1;
+  }
+  const int n_teams = (int)team_size.size();
+  std::vector<int32_t> cta_team(used), cta_rank(used), tsize(n_teams), tptr(n_teams + 1, 0), tlist;
+  int c = 0;
+  for (int t = 0; t < n_teams; ++t) {
+    tsize[t] = team_size[t];
+    for (int r = 0; r < team_size[t]; ++r) {
+      cta_team[c] = t;
+      cta_rank[c] = r;
+      ++c;
+    }
+    for (int k : team_inst[t]) tlist.push_back(k);
+    tptr[t + 1] = (int32_t)tlist.size();
+  }
+  b->grid = used;
+  b->n_teams = n_teams;
+  // ---- one device table block
+  Carver cv;
+  auto layout = [&](Carver &C) {
+    b->d_insts = C.take<Inst>(n);
+    b->d_tiles64 = C.take<Tile>(t64.size());
+    b->d_tiles32 = C.take<Tile>(t32.size());
+    b->sched.cta_team = C.take<int32_t>(used);
+    b->sched.cta_rank = C.take<int32_t>(used);
+    b->sched.team_size = C.take<int32_t>(n_teams);
+    b->sched.team_ptr = C.take<int32_t>(n_teams + 1);
+    b->sched.team_list = C.take<int32_t>(tlist.size());
+    b->sched.bar = C.take<unsigned int>((size_t)32 * n_teams);
+    b->sched.abort_flag = C.take<int32_t>(1);
+    b->d_status_out = C.take<InstStatus>(n);
+    b->d_abort_out = C.take<int32_t>(1);
+  };
+  layout(cv);
+  if (cv.off > b->tbl_bytes) {
+    if (b->tbl) b->mem.put(b->tbl, b->tbl_bytes);
+    b->tbl_bytes = cv.off + 4096;
+    b->tbl = b->mem.get(b->tbl_bytes);
+    if (!b->tbl) {
+      b->tbl_bytes = 0;
+      return SHELL_ERR_OOM;
+    }
+  }
+  Carver real;
+  real.base = (char *)b->tbl;
+  layout(real);
+  b->sched.n_ctas = used;
+  cudaStream_t st = b->mem.st;
+  CK(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
+  if (!t64.empty()) CK(cudaMemcpyAsync(b->d_tiles64, t64.data(), sizeof(Tile) * t64.size(), cudaMemcpyHostToDevice, st));
+  if (!t32.empty()) CK(cudaMemcpyAsync(b->d_tiles32, t32.data(), sizeof(Tile) * t32.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.cta_team, cta_team.data(), 4 * used, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.cta_rank, cta_rank.data(), 4 * used, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.team_ptr, tptr.data(), 4 * (n_teams + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.team_list, tlist.data(), 4 * tlist.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * 32 * n_teams, st));
+  CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
+  CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
+  b->n_tiles64 = (int)t64.size();
+  b->n_tiles32 = (int)t32.size();
+  b->dirty = false;
+  return SHELL_OK;
+}
+
+int launch_step(shell_batch *b) {
+  cudaStream_t st = b->mem.st;
+  CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
+  CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
+  CK(launch_solve(b->d_insts, b->sched, b->grid, st));
+  return SHELL_OK;
+}
+
+// capture one step into a CUDA graph (falls back to direct launches if capture is refused)
+void try_capture(shell_batch *b) {
+  b->graph_tried = true;
+  cudaStream_t st = b->mem.st;
+  if (st == nullptr) return;   // the legacy default stream cannot be captured
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  int rc = launch_step(b);
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != SHELL_OK || e != cudaSuccess || !g) {
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    return;
+  }
+  if (cudaGraphInstantiate(&b->gexec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    b->gexec = nullptr;
+  }
+  cudaGraphDestroy(g);
+}
+
+int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
+  if (n_steps < 0) return SHELL_ERR_INVALID_ARG;
+  if (b->dirty) {
+    int rc = rebuild_tables(b);
+    if (rc != SHELL_OK) return rc;
+  }
+  const int n = b->n_active;
+  if (n == 0 || n_steps == 0) {
+    if (stats)
+      for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0};
+    return SHELL_OK;
+  }
+  cudaStream_t st = b->mem.st;
+  // statuses before the call (cumulative counters)
+  std::vector<InstStatus> before(n), after(n);
+  for (int k = 0; k < n; ++k) before[k] = b->slots[b->active[k]]->last_status;
+  if (!b->graph_tried) try_capture(b);
+  const int n_ev = std::min(n_steps, 4096) + 1;
+  while ((int)b->events.size() < n_ev) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    b->events.push_back(e);
+  }
+  const int ev_stride = (n_steps + n_ev - 2) / (n_ev - 1);
+  int ev = 0;
+  CK(cudaEventRecord(b->events[ev++], st));
+  const int n_prof = b->profiling ? std::min(n_steps, 4096) : 0;
+  while ((int)b->pev.size() < 3 * n_prof) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    b->pev.push_back(e);
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    if (s < n_prof) {
+      CK(cudaEventRecord(b->pev[3 * s], st));
+      CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
+      CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
+      CK(cudaEventRecord(b->pev[3 * s + 1], st));
+      CK(launch_solve(b->d_insts, b->sched, b->grid, st));
+      CK(cudaEventRecord(b->pev[3 * s + 2], st));
+    } else if (b->gexec) {
+      CK(cudaGraphLaunch(b->gexec, st));
+    } else {
+      int rc = launch_step(b);
+      if (rc != SHELL_OK) return rc;
+    }
+    if ((s + 1) % ev_stride == 0 && ev < n_ev) CK(cudaEventRecord(b->events[ev++], st));
+  }
+  CK(launch_gather_status(b->d_insts, n, b->d_status_out, b->sched.abort_flag, b->d_abort_out, st));
+  int32_t aborted = 0;
+  CK(cudaMemcpyAsync(after.data(), b->d_status_out, sizeof(InstStatus) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&aborted, b->d_abort_out, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  b->kern_ms[0] = b->kern_ms[1] = 0.0;
+  for (int s = 0; s < n_prof; ++s) {
+    float f = 0.f, v = 0.f;
+    cudaEventElapsedTime(&f, b->pev[3 * s], b->pev[3 * s + 1]);
+    cudaEventElapsedTime(&v, b->pev[3 * s + 1], b->pev[3 * s + 2]);
+    b->kern_ms[0] += f;
+    b->kern_ms[1] += v;
+  }
+  b->step_ms.clear();
+  for (int k = 1; k < ev; ++k) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, b->events[k - 1], b->events[k]);
+    b->step_ms.push_back(ms / ev_stride);
+  }
+  int first_err = SHELL_OK;
+  if (aborted) {
+    first_err = SHELL_ERR_TIMEOUT;
+    CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * 32 * b->n_teams, st));
+    CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
+    CK(cudaStreamSynchronize(st));
+  }
+  if (stats)
+    for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0};
+  for (int k = 0; k < n; ++k) {
+    shell_handle *h = b->slots[b->active[k]];
+    const InstStatus &a = after[k];
+    const InstStatus &z = before[k];
+    h->last_status = a;
+    const int done = a.steps_done - z.steps_done;
+    if (a.err != SHELL_OK && first_err == SHELL_OK) first_err = a.err;
+    if (done > 0) {
+      const double it = a.last_iters + 2.0 * a.last_rounds;
+      h->est_iters = 0.5 * h->est_iters + 0.5 * std::max(1.0, it);
+    }
+    if (stats) {
+      shell_step_stats &o = stats[b->active[k]];
+      o.steps_done = done;
+      o.pcg_iterations = a.last_iters;
+      o.refine_rounds = a.last_rounds;
+      o.status = a.err;
+      o.total_pcg_iterations = a.total_iters - z.total_iters;
+      o.rel_residual = a.rel_res;
+      o.total_refine_rounds = a.total_rounds - z.total_rounds;
+    }
+  }
+  return first_err;
+}
+
+int batch_new(const shell_options *opt, size_t budget, bool solo, shell_batch **out) {
+  shell_batch *b = new (std::nothrow) shell_batch();
+  if (!b) return SHELL_ERR_OOM;
+  b->opt = *opt;
+  b->mem.alloc = opt->alloc;
+  b->mem.free = opt->free;
+  b->mem.user = opt->alloc_user;
+  b->mem.st = (cudaStream_t)opt->cuda_stream;
+  b->budget = budget;
+  b->solo = solo;
+  *out = b;
+  return SHELL_OK;
+}
+
+void batch_free(shell_batch *b) {
+  if (!b) return;
+  destroy_graph(b);
+  for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->pev) cudaEventDestroy(e);
+  if (b->tbl) b->mem.put(b->tbl, b->tbl_bytes);
+  for (shell_handle *h : b->slots)
+    if (h && !b->solo) {
+      h->batch = nullptr;
+      h->slot = -1;
+    }
+  delete b;
+}
+
+void fill_default_tolerances(shell_options *o) {
+  if (!(o->pcg_rtol > 0.0)) o->pcg_rtol = (o->precision == SHELL_FP64) ? 1e-13 : 1e-4;
+  if (!(o->refine_rtol > 0.0)) o->refine_rtol = 1e-10;
+  if (o->pcg_max_it <= 0) o->pcg_max_it = 20000;
+  if (o->refine_max <= 0) o->refine_max = 20;
+}
+
+bool planar(const double *X, int nv, const int32_t *tris, int nt) {
+  // normal of the largest triangle; every vertex within 1e-9 * extent of its plane
+  double best = -1.0, n[3] = {0, 0, 1};
+  const double *o = X;
+  for (int t = 0; t < nt; ++t) {
+    const double *a = X + 3 * tris[3 * t], *b = X + 3 * tris[3 * t + 1], *c = X + 3 * tris[3 * t + 2];
+    double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double w[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    double l = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (l > best) {
+      best = l;
+      n[0] = w[0] / l;
+      n[1] = w[1] / l;
+      n[2] = w[2] / l;
+      o = a;
+    }
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < nv; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], X[3 * i + c]);
+      hi[c] = std::max(hi[c], X[3 * i + c]);
+    }
+  double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  for (int i = 0; i < nv; ++i) {
+    double d = (X[3 * i] - o[0]) * n[0] + (X[3 * i + 1] - o[1]) * n[1] + (X[3 * i + 2] - o[2]) * n[2];
+    if (std::fabs(d) > 1e-9 * ext) return false;
+  }
+  return true;
+}
+
+std::vector<double> to_soa(const double *aos, int nv) {
+  std::vector<double> s((size_t)3 * nv);
+  for (int i = 0; i < nv; ++i)
+    for (int c = 0; c < 3; ++c) s[(size_t)c * nv + i] = aos[3 * i + c];
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+void shell_default_options(shell_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dt = 1e-2;
+  o->precision = SHELL_FP64;
+  o->pcg_rtol = 0.0;      // precision default: 1e-13 (FP64) / 1e-4 (FP32 inner)
+  o->refine_rtol = 0.0;   // 1e-10
+  o->pcg_max_it = 20000;
+  o->refine_max = 20;
+}
+
+const char *shell_strerror(int code) {
+  switch (code) {
+    case SHELL_OK: return "ok";
+    case SHELL_ERR_INVALID_ARG: return "invalid argument";
+    case SHELL_ERR_NON_MANIFOLD: return "mesh is not manifold";
+    case SHELL_ERR_BAD_ORIENTATION: return "triangles are not consistently oriented";
+    case SHELL_ERR_DEGENERATE: return "degenerate rest triangle or stencil";
+    case SHELL_ERR_SINGULAR_OPERATOR: return "singular smoothed-hinge fit (L_p C_p)";
+    case SHELL_ERR_OOM: return "device memory allocation failed";
+    case SHELL_ERR_BUDGET: return "batch memory budget exceeded";
+    case SHELL_ERR_NOT_CONVERGED: return "linear solve did not converge within its iteration cap";
+    case SHELL_ERR_NONFINITE: return "non-finite value in the step";
+    case SHELL_ERR_TIMEOUT: return "device-side wait timed out";
+    case SHELL_ERR_CUDA: return cudaGetErrorString(last_cuda_error());
+    case SHELL_ERR_NO_DEVICE: return "no CUDA device of compute capability 10.3";
+    case SHELL_ERR_BUSY: return "handle is resident in a batch";
+    default: return "unknown error";
+  }
+}
+
+int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t model, const shell_bc *bc,
+                 const shell_options *opt_in, shell_handle **out) {
+  if (!mesh || !mat || !out || !mesh->tris || !mesh->rest_xyz) return SHELL_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (mesh->n_verts < 3 || mesh->n_tris < 1) return SHELL_ERR_INVALID_ARG;
+  if (model < SHELL_EP || model > SHELL_SS) return SHELL_ERR_INVALID_ARG;
+  if (!(mat->E > 0) || !(mat->nu >= 0 && mat->nu < 0.5) || !(mat->thickness > 0) || !(mat->density > 0))
+    return SHELL_ERR_INVALID_ARG;
+  shell_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else
+    shell_default_options(&opt);
+  if (!(opt.dt > 0) || (opt.precision != SHELL_FP64 && opt.precision != SHELL_FP32_REFINE))
+    return SHELL_ERR_INVALID_ARG;
+  fill_default_tolerances(&opt);
+  const int nv = mesh->n_verts, nt = mesh->n_tris;
+  if (bc && ((bc->n_clamped > 0 && !bc->clamped_edges) || (bc->n_loads > 0 && (!bc->load_vtx || !bc->load_f))))
+    return SHELL_ERR_INVALID_ARG;
+  if (bc)
+    for (int k = 0; k < bc->n_loads; ++k)
+      if (bc->load_vtx[k] < 0 || bc->load_vtx[k] >= nv) return SHELL_ERR_INVALID_ARG;
+  int rc = check_device();
+  if (rc != SHELL_OK) return rc;
+
+  const bool plate = (model == SHELL_EP || model == SHELL_FP || model == SHELL_SP);
+  if (plate && !planar(mesh->rest_xyz, nv, mesh->tris, nt)) return SHELL_ERR_INVALID_ARG;
+
+  HostTopo T;
+  rc = build_topology(nv, nt, mesh->tris, bc ? bc->n_clamped : 0, bc ? bc->clamped_edges : nullptr, model, &T);
+  if (rc != SHELL_OK) return rc;
+
+  shell_handle *h = new (std::nothrow) shell_handle();
+  if (!h) return SHELL_ERR_OOM;
+  h->nv = nv;
+  h->nt = nt;
+  h->ne = T.ne;
+  h->model = model;
+  h->mat = *mat;
+  h->opt = opt;
+  h->mem.alloc = opt.alloc;
+  h->mem.free = opt.free;
+  h->mem.user = opt.alloc_user;
+  h->mem.st = (cudaStream_t)opt.cuda_stream;
+  cudaStream_t st = h->mem.st;
+
+  Inst &I = h->h;
+  I.nv = nv;
+  I.nt = nt;
+  I.ne = T.ne;
+  I.model = model;
+  I.precision = opt.precision;
+  I.kt = T.kt;
+  I.n_slices = T.n_slices;
+  I.rows_per_thread = nv > (1 << 20) ? 4 : (nv > (1 << 16) ? 2 : 1);
+  const int chunk = kBlock * I.rows_per_thread;
+  I.n_chunks = (nv + chunk - 1) / chunk;
+  I.pcg_max_it = opt.pcg_max_it;
+  I.refine_max = opt.refine_max;
+  I.dt = opt.dt;
+  I.pcg_rtol = opt.pcg_rtol;
+  I.refine_rtol = opt.refine_rtol;
+  I.mu = mat->E / (2.0 * (1.0 + mat->nu));
+  I.lam = mat->E * mat->nu / (1.0 - mat->nu * mat->nu);
+  I.n_slots = T.n_slots;
+  I.n_local = T.n_local;
+  const size_t nnz_pad = (size_t)T.sl_ptr[T.n_slices];
+  h->nnz = T.nnz;
+  h->nnz_pad = (int64_t)nnz_pad;
+  const int ne = T.ne;
+  const int n_loads = bc ? bc->n_loads : 0;
+
+  for (int s0 = 0; s0 < nt; s0 += kForceBlock) h->tiles.push_back({0, 0, s0, std::min(kForceBlock, nt - s0)});
+  for (int s0 = 0; s0 < ne; s0 += kForceBlock) h->tiles.push_back({0, 1, s0, std::min(kForceBlock, ne - s0)});
+
+  // ---- persistent block
+  auto layout = [&](Carver &C) {
+    I.x = C.take<double>(3 * (size_t)nv);
+    I.v = C.take<double>(3 * (size_t)nv);
+    I.rest = C.take<double>(3 * (size_t)nv);
+    I.fext = C.take<double>(3 * (size_t)nv);
+    I.mass = C.take<double>(nv);
+    I.pinned = C.take<uint8_t>(nv);
+    I.t_idx = C.take<int32_t>(6 * (size_t)nt);
+    I.t_bc = C.take<uint8_t>(3 * (size_t)nt);
+    I.t_mode = C.take<uint8_t>(nt);
+    I.t_L64 = C.take<double>(18 * (size_t)nt);
+    I.t_L32 = C.take<float>(18 * (size_t)nt);
+    I.t_W64 = C.take<double>(6 * (size_t)nt);
+    I.t_W32 = C.take<float>(6 * (size_t)nt);
+    I.t_k064 = C.take<double>(3 * (size_t)nt);
+    I.t_k032 = C.take<float>(3 * (size_t)nt);
+    I.t_n64 = C.take<double>(3 * (size_t)nt);
+    I.t_n32 = C.take<float>(3 * (size_t)nt);
+    I.m_D64 = C.take<double>(3 * (size_t)nt);
+    I.m_D32 = C.take<float>(3 * (size_t)nt);
+    I.m_G64 = C.take<double>(3 * (size_t)nt);
+    I.m_At64 = C.take<double>(nt);
+    I.m_At32 = C.take<float>(nt);
+    I.e_idx = C.take<int32_t>(4 * (size_t)ne);
+    I.e_mode = C.take<uint8_t>(ne);
+    I.e_L64 = C.take<double>(4 * (size_t)ne);
+    I.e_L32 = C.take<float>(4 * (size_t)ne);
+    I.e_w64 = C.take<double>(ne);
+    I.e_w32 = C.take<float>(ne);
+    I.e_k064 = C.take<double>(ne);
+    I.e_k032 = C.take<float>(ne);
+    I.e_n64 = C.take<double>(3 * (size_t)ne);
+    I.e_n32 = C.take<float>(3 * (size_t)ne);
+    I.vtx_ptr = C.take<int32_t>(nv + 1);
+    I.vtx_slot = C.take<int32_t>(T.vtx_slot.size());
+    I.contrib = C.take<double>(3 * (size_t)T.n_slots);
+    I.sl_ptr = C.take<int32_t>(T.n_slices + 1);
+    I.sl_col = C.take<int32_t>(nnz_pad);
+    I.val64 = C.take<double>(nnz_pad);
+    I.val32 = C.take<float>(nnz_pad);
+    I.dinv64 = C.take<double>(nv);
+    I.dinv32 = C.take<float>(nv);
+    I.diag_pos = C.take<int32_t>(nv);
+    I.b = C.take<double>(3 * (size_t)nv);
+    I.sol = C.take<double>(3 * (size_t)nv);
+    I.r64 = C.take<double>(3 * (size_t)nv);
+    I.g64 = C.take<double>(4 * (size_t)nv);
+    I.r = C.take<double>(3 * (size_t)nv);
+    I.p = C.take<double>(3 * (size_t)nv);
+    I.s = C.take<double>(3 * (size_t)nv);
+    I.w = C.take<double>(3 * (size_t)nv);
+    I.xs = C.take<double>(3 * (size_t)nv);
+    I.g = C.take<double>(4 * (size_t)nv);
+    I.part = C.take<double>(8 * (size_t)I.n_chunks);
+    I.ebuf = C.take<double>(2 * (size_t)(nt + ne));
+    I.status = C.take<InstStatus>(1);
+    I.err_flags = C.take<int32_t>(1);
+    h->d_inst = C.take<Inst>(1);
+    h->d_stage = C.take<double>(6 * (size_t)nv);
+    h->d_energy = C.take<double>(4);
+    h->d_forces = h->d_stage;   // shares the staging area
+    h->d_tiles = C.take<Tile>(h->tiles.size());
+  };
+  Carver sizer;
+  layout(sizer);
+  h->block_bytes = sizer.off;
+  h->block = h->mem.get(h->block_bytes);
+  if (!h->block) {
+    delete h;
+    return SHELL_ERR_OOM;
+  }
+  Carver real;
+  real.base = (char *)h->block;
+  layout(real);
+
+  // ---- temporary block: assembly sources, local matrices, point loads
+  int32_t *d_lv = nullptr;
+  double *d_lf = nullptr;
+  auto tlayout = [&](Carver &C) {
+    I.asm_ptr = C.take<int32_t>(nnz_pad + 1);
+    I.asm_src = C.take<int32_t>(T.asm_src.size());
+    I.local = C.take<double>(T.n_local);
+    d_lv = C.take<int32_t>(n_loads);
+    d_lf = C.take<double>(3 * (size_t)n_loads);
+  };
+  Carver tsz;
+  tlayout(tsz);
+  void *tmp = h->mem.get(tsz.off);
+  if (!tmp) {
+    h->mem.put(h->block, h->block_bytes);
+    delete h;
+    return SHELL_ERR_OOM;
+  }
+  Carver treal;
+  treal.base = (char *)tmp;
+  tlayout(treal);
+
+  auto fail = [&](int code) {
+    cudaStreamSynchronize(st);
+    h->mem.put(tmp, tsz.off);
+    h->mem.put(h->block, h->block_bytes);
+    delete h;
+    return code;
+  };
+#define CKF(call)                     \
+  do {                                \
+    cudaError_t e_ = (call);          \
+    if (e_ != cudaSuccess) {          \
+      last_cuda_error() = e_;         \
+      return fail(SHELL_ERR_CUDA);    \
+    }                                 \
+  } while (0)
+
+  // ---- uploads
+  std::vector<double> rest = to_soa(mesh->rest_xyz, nv);
+  std::vector<double> x0 = to_soa(mesh->init_xyz ? mesh->init_xyz : mesh->rest_xyz, nv);
+  std::vector<double> v0 = mesh->init_vel ? to_soa(mesh->init_vel, nv) : std::vector<double>((size_t)3 * nv, 0.0);
+  std::vector<uint8_t> pin(nv, 0);
+  if (bc && bc->pinned)
+    for (int i = 0; i < nv; ++i) pin[i] = bc->pinned[i] ? 1 : 0;
+  if (bc)
+    for (int k = 0; k < 2 * bc->n_clamped; ++k) pin[bc->clamped_edges[k]] = 1;
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  CKF(up(I.rest, rest.data(), 8 * rest.size()));
+  CKF(up(I.x, x0.data(), 8 * x0.size()));
+  CKF(up(I.v, v0.data(), 8 * v0.size()));
+  CKF(up(I.pinned, pin.data(), nv));
+  CKF(up(I.t_idx, T.t_idx.data(), 4 * T.t_idx.size()));
+  CKF(up(I.t_bc, T.t_bc.data(), T.t_bc.size()));
+  CKF(up(I.e_idx, T.e_idx.data(), 4 * T.e_idx.size()));
+  CKF(up(I.vtx_ptr, T.vtx_ptr.data(), 4 * T.vtx_ptr.size()));
+  CKF(up(I.vtx_slot, T.vtx_slot.data(), 4 * T.vtx_slot.size()));
+  CKF(up(I.sl_ptr, T.sl_ptr.data(), 4 * T.sl_ptr.size()));
+  CKF(up(I.sl_col, T.sl_col.data(), 4 * T.sl_col.size()));
+  CKF(up(I.diag_pos, T.diag_pos.data(), 4 * T.diag_pos.size()));
+  CKF(up(I.asm_ptr, T.asm_ptr.data(), 4 * T.asm_ptr.size()));
+  CKF(up(I.asm_src, T.asm_src.data(), 4 * T.asm_src.size()));
+  if (n_loads) {
+    CKF(up(d_lv, bc->load_vtx, 4 * (size_t)n_loads));
+    CKF(up(d_lf, bc->load_f, 24 * (size_t)n_loads));
+  }
+  CKF(cudaMemsetAsync(I.val64, 0, 8 * nnz_pad, st));
+  CKF(cudaMemsetAsync(I.val32, 0, 4 * nnz_pad, st));
+  CKF(cudaMemsetAsync(I.t_mode, MODE_NONE, nt, st));
+  CKF(cudaMemsetAsync(I.status, 0, sizeof(InstStatus), st));
+  CKF(cudaMemsetAsync(I.err_flags, 0, sizeof(int32_t), st));
+  CKF(cudaMemsetAsync(I.g, 0, 32 * (size_t)nv, st));
+  CKF(cudaMemsetAsync(I.g64, 0, 32 * (size_t)nv, st));
+  CKF(up(h->d_inst, &I, sizeof(Inst)));
+  CKF(up(h->d_tiles, h->tiles.data(), sizeof(Tile) * h->tiles.size()));
+  // ---- device precompute and assembly (FP64)
+  const double g[3] = {bc ? bc->gravity[0] : 0.0, bc ? bc->gravity[1] : 0.0, bc ? bc->gravity[2] : 0.0};
+  CKF(launch_precompute(h->d_inst, I, mat->E, mat->nu, mat->thickness, mat->density, st));
+  CKF(launch_mass(h->d_inst, I, mat->density, g, n_loads, d_lv, d_lf, st));
+  CKF(launch_assemble(h->d_inst, I, st));
+  int32_t flags = 0;
+  CKF(cudaMemcpyAsync(&flags, I.err_flags, 4, cudaMemcpyDeviceToHost, st));
+  CKF(cudaStreamSynchronize(st));
+  h->mem.put(tmp, tsz.off);
+  I.asm_ptr = nullptr;
+  I.asm_src = nullptr;
+  I.local = nullptr;
+  cudaMemcpyAsync(h->d_inst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  if (flags) {
+    h->mem.put(h->block, h->block_bytes);
+    delete h;
+    return (flags & 1) ? SHELL_ERR_DEGENERATE : SHELL_ERR_SINGULAR_OPERATOR;
+  }
+#undef CKF
+  // ---- private batch for shell_step
+  rc = batch_new(&opt, (size_t)-1, true, &h->solo);
+  if (rc != SHELL_OK) {
+    h->mem.put(h->block, h->block_bytes);
+    delete h;
+    return rc;
+  }
+  h->solo->slots.push_back(h);
+  *out = h;
+  return SHELL_OK;
+}
+
+int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
+  if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
+  if (h->batch) return SHELL_ERR_BUSY;
+  return batch_step(h->solo, n_steps, stats);
+}
+
+static int run_forces64(shell_handle *h, int want_energy) {
+  cudaStream_t st = h->mem.st;
+  cudaError_t e = launch_forces(h->d_inst, h->d_tiles, (int)h->tiles.size(), want_energy, 0, st);
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return SHELL_ERR_CUDA;
+  }
+  return SHELL_OK;
+}
+
+int shell_energy(shell_handle *h, double out[4]) {
+  if (!h || !out) return SHELL_ERR_INVALID_ARG;
+  int rc = run_forces64(h, 1);
+  if (rc != SHELL_OK) return rc;
+  cudaStream_t st = h->mem.st;
+  CK(launch_energy_reduce(h->d_inst, h->h, h->d_energy, st));
+  CK(cudaMemcpyAsync(out, h->d_energy, 32, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_forces(shell_handle *h, double *out_xyz) {
+  if (!h || !out_xyz) return SHELL_ERR_INVALID_ARG;
+  int rc = run_forces64(h, 0);
+  if (rc != SHELL_OK) return rc;
+  cudaStream_t st = h->mem.st;
+  CK(launch_gather_forces(h->d_inst, h->h, h->d_forces, st));
+  CK(cudaMemcpyAsync(out_xyz, h->d_forces, 24 * (size_t)h->nv, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_apply_matrix(shell_handle *h, const double *in, double *out) {
+  if (!h || !in || !out) return SHELL_ERR_INVALID_ARG;
+  cudaStream_t st = h->mem.st;
+  const size_t n3 = 3 * (size_t)h->nv;
+  CK(cudaMemcpyAsync(h->d_stage, in, 8 * n3, cudaMemcpyHostToDevice, st));
+  CK(launch_matvec64(h->d_inst, h->h, h->d_stage, h->d_stage + n3, st));
+  CK(cudaMemcpyAsync(out, h->d_stage + n3, 8 * n3, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_get_state(shell_handle *h, double *x, double *v) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  cudaStream_t st = h->mem.st;
+  const size_t n3 = 3 * (size_t)h->nv;
+  if (x) {
+    CK(launch_soa_to_aos(h->h.x, h->d_stage, h->nv, st));
+    CK(cudaMemcpyAsync(x, h->d_stage, 8 * n3, cudaMemcpyDeviceToHost, st));
+  }
+  if (v) {
+    CK(launch_soa_to_aos(h->h.v, h->d_stage + n3, h->nv, st));
+    CK(cudaMemcpyAsync(v, h->d_stage + n3, 8 * n3, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_set_state(shell_handle *h, const double *x, const double *v) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  cudaStream_t st = h->mem.st;
+  const size_t n3 = 3 * (size_t)h->nv;
+  if (x) {
+    CK(cudaMemcpyAsync(h->d_stage, x, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(launch_aos_to_soa(h->d_stage, h->h.x, h->nv, st));
+  }
+  if (v) {
+    CK(cudaMemcpyAsync(h->d_stage + n3, v, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(launch_aos_to_soa(h->d_stage + n3, h->h.v, h->nv, st));
+  }
+  // a new state clears a previous step failure
+  CK(cudaMemsetAsync(&h->h.status->err, 0, sizeof(int32_t), st));
+  h->last_status.err = SHELL_OK;
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_get_state_device(shell_handle *h, double *d_x, double *d_v) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  cudaStream_t st = h->mem.st;
+  if (d_x) CK(launch_soa_to_aos(h->h.x, d_x, h->nv, st));
+  if (d_v) CK(launch_soa_to_aos(h->h.v, d_v, h->nv, st));
+  return SHELL_OK;
+}
+
+int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  cudaStream_t st = h->mem.st;
+  if (d_x) CK(launch_aos_to_soa(d_x, h->h.x, h->nv, st));
+  if (d_v) CK(launch_aos_to_soa(d_v, h->h.v, h->nv, st));
+  return SHELL_OK;
+}
+
+int shell_info(shell_handle *h, int64_t out[7]) {
+  if (!h || !out) return SHELL_ERR_INVALID_ARG;
+  out[0] = h->nv;
+  out[1] = h->nt;
+  out[2] = (h->model == SHELL_EP || h->model == SHELL_ES) ? h->ne : h->nt;
+  out[3] = (int64_t)h->block_bytes;
+  out[4] = h->nnz;
+  out[5] = h->nnz_pad;
+  out[6] = h->h.n_slots;
+  return SHELL_OK;
+}
+
+int shell_destroy(shell_handle *h) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  if (h->batch) return SHELL_ERR_BUSY;
+  cudaStreamSynchronize(h->mem.st);
+  batch_free(h->solo);
+  h->mem.put(h->block, h->block_bytes);
+  cudaStreamSynchronize(h->mem.st);
+  delete h;
+  return SHELL_OK;
+}
+
+int shell_topology_summary(int32_t nv, int32_t nt, const int32_t *tris, int32_t n_clamped, const int32_t *clamped,
+                           int32_t model, int64_t out[8]) {
+  if (!tris || !out || nv < 3 || nt < 1 || model < SHELL_EP || model > SHELL_SS) return SHELL_ERR_INVALID_ARG;
+  if (n_clamped > 0 && !clamped) return SHELL_ERR_INVALID_ARG;
+  HostTopo T;
+  int rc = build_topology(nv, nt, tris, n_clamped, clamped, model, &T);
+  if (rc != SHELL_OK) return rc;
+  int64_t bad = 0;
+  int64_t virt = 0;
+  for (int t = 0; t < nt; ++t) {
+    bool v = false;
+    for (int j = 0; j < 6; ++j) {
+      int q = T.t_idx[(size_t)j * nt + t];
+      if (q >= nv || (j < 3 && q < 0) || q < -1) ++bad;
+      if (j >= 3 && q < 0) {
+        v = true;
+        if (T.t_bc[(size_t)(j - 3) * nt + t] == 0) ++bad;
+      }
+      if (j >= 3 && q >= 0 && T.t_bc[(size_t)(j - 3) * nt + t] != 0) ++bad;
+    }
+    virt += v;
+  }
+  for (int e = 0; e < T.ne; ++e)
+    for (int j = 0; j < 4; ++j) {
+      int q = T.e_idx[(size_t)j * T.ne + e];
+      if (q >= nv || q < (j == 3 ? -1 : 0)) ++bad;
+      if (j == 3 && (q < 0) != (e >= T.ne_int)) ++bad;
+    }
+  if ((int)T.vtx_ptr.size() != nv + 1 || T.vtx_ptr[0] != 0) ++bad;
+  for (int i = 0; i < nv && !bad; ++i)
+    for (int q = T.vtx_ptr[i]; q < T.vtx_ptr[i + 1]; ++q)
+      if (T.vtx_slot[q] < 0 || T.vtx_slot[q] >= T.n_slots || (q > T.vtx_ptr[i] && T.vtx_slot[q] <= T.vtx_slot[q - 1]))
+        ++bad;
+  const int64_t nnz_pad = T.sl_ptr[T.n_slices];
+  for (int s = 0; s < T.n_slices; ++s)
+    if ((T.sl_ptr[s + 1] - T.sl_ptr[s]) % 32 != 0) ++bad;
+  for (int64_t p = 0; p < nnz_pad; ++p)
+    if (T.sl_col[p] < 0 || T.sl_col[p] >= nv) ++bad;
+  for (int i = 0; i < nv; ++i) {
+    int d = T.diag_pos[i];
+    int s = i / 32;
+    if (d < T.sl_ptr[s] || d >= T.sl_ptr[s + 1] || T.sl_col[d] != i || (d - T.sl_ptr[s]) % 32 != i % 32) ++bad;
+  }
+  if ((int64_t)T.asm_ptr.size() != nnz_pad + 1 || T.asm_ptr[nnz_pad] != (int64_t)T.asm_src.size()) ++bad;
+  for (int32_t q : T.asm_src)
+    if (q < 0 || q >= T.n_local) ++bad;
+  out[0] = T.ne_int;
+  out[1] = T.ne - T.ne_int;
+  out[2] = virt;
+  out[3] = T.nnz;
+  out[4] = nnz_pad;
+  out[5] = T.n_slots;
+  out[6] = (int64_t)T.asm_src.size();
+  out[7] = bad;
+  return SHELL_OK;
+}
+
+// ---------------------------------------------------------------- batches
+int shell_batch_create(const shell_options *opt, size_t budget, shell_batch **out) {
+  if (!out) return SHELL_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_device();
+  if (rc != SHELL_OK) return rc;
+  shell_options o;
+  if (opt)
+    o = *opt;
+  else
+    shell_default_options(&o);
+  return batch_new(&o, budget, false, out);
+}
+
+int shell_batch_admit(shell_batch *b, shell_handle *h, int32_t *slot) {
+  if (!b || !h) return SHELL_ERR_INVALID_ARG;
+  if (h->batch) return SHELL_ERR_BUSY;
+  if (b->used + h->block_bytes > b->budget) return SHELL_ERR_BUDGET;
+  int k = -1;
+  for (size_t q = 0; q < b->slots.size(); ++q)
+    if (!b->slots[q]) {
+      k = (int)q;
+      break;
+    }
+  if (k < 0) {
+    k = (int)b->slots.size();
+    b->slots.push_back(nullptr);
+  }
+  b->slots[k] = h;
+  h->batch = b;
+  h->slot = k;
+  b->used += h->block_bytes;
+  b->dirty = true;
+  if (slot) *slot = k;
+  return SHELL_OK;
+}
+
+int shell_batch_retire(shell_batch *b, int32_t slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot]) return SHELL_ERR_INVALID_ARG;
+  shell_handle *h = b->slots[slot];
+  cudaStreamSynchronize(b->mem.st);
+  b->slots[slot] = nullptr;
+  h->batch = nullptr;
+  h->slot = -1;
+  b->used -= h->block_bytes;
+  b->dirty = true;
+  return SHELL_OK;
+}
+
+int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  return batch_step(b, n_steps, stats);
+}
+
+int shell_batch_capacity(shell_batch *b) { return b ? (int)b->slots.size() : 0; }
+
+int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n) {
+  if (!b || !out_ms || n < 0) return SHELL_ERR_INVALID_ARG;
+  for (int k = 0; k < n && k < (int)b->step_ms.size(); ++k) out_ms[k] = b->step_ms[k];
+  return std::min<int>(n, (int)b->step_ms.size());
+}
+
+int shell_batch_set_profiling(shell_batch *b, int32_t on) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  b->profiling = on != 0;
+  return SHELL_OK;
+}
+
+int shell_batch_kernel_times(shell_batch *b, double out_ms[2]) {
+  if (!b || !out_ms) return SHELL_ERR_INVALID_ARG;
+  out_ms[0] = b->kern_ms[0];
+  out_ms[1] = b->kern_ms[1];
+  return SHELL_OK;
+}
+
+int shell_batch_destroy(shell_batch *b) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  cudaStreamSynchronize(b->mem.st);
+  batch_free(b);
+  return SHELL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// internal.h -- device-side data layout of the thin plate / shell library (not part of the public ABI).
+//
+// One simulation ("instance") owns one device block holding everything below. All per-vertex vectors are
+// structure-of-arrays [3][nv] (coalesced per-row access) except the vector the SpMV gathers, which is
+// array-of-structures [nv][4] so one gather is one 16-byte (FP32) or two 16-byte (FP64) loads.
+// The matrix is the scalar constant matrix A = M + dt^2 (K_b + K_m) (every 3x3 block of the bending and
+// membrane Hessians is a multiple of I_3, Eq. 21 / 41 / 53), stored as SELL-32: slices of 32 rows,
+// column-major inside a slice, width = the longest row of the slice.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/shell.h"
+
+namespace shl {
+
+constexpr int kSlice = 32;          // SELL slice height (one warp)
+constexpr int kBlock = 256;         // threads of every CTA of the persistent solve kernel
+constexpr int kForceBlock = 128;    // threads of a force tile
+constexpr int kMaxTeamWaitMs = 4000;  // bounded spin of the team barrier
+
+// stencil modes
+enum : uint8_t { MODE_PLATE = 0, MODE_SHELL = 1, MODE_FIXED = 2, MODE_NONE = 3 };
+// boundary code of a triangle-stencil hinge
+enum : uint8_t { BC_INTERIOR = 0, BC_FREE = 1, BC_CLAMPED = 2 };
+
+struct InstStatus {
+  int32_t err;          // SHELL_OK or the code that stopped this instance
+  int32_t steps_done;   // committed steps (cumulative; the host takes differences)
+  int32_t last_iters;   // PCG iterations of the last committed step
+  int32_t last_rounds;  // refinement rounds of the last committed step
+  long long total_iters;
+  double rel_res;       // relative residual of the last committed step
+  int32_t fail_step;    // steps_done when the failure happened
+  int32_t pad;
+  long long total_rounds;
+};
+
+// Per-instance device descriptor (lives in device memory; every pointer is a device pointer).
+struct Inst {
+  // sizes and parameters
+  int32_t nv, nt, ne;            // vertices, triangles, edge stencils (interior + clamped)
+  int32_t model;                 // shell_model
+  int32_t precision;             // shell_precision
+  int32_t kt;                    // contribution slots per triangle: 6 (triangle stencils) or 3 (membrane only)
+  int32_t n_slices;              // SELL slices
+  int32_t rows_per_thread;       // rows per thread of a reduction chunk (chunk = kBlock * rows_per_thread)
+  int32_t n_chunks;
+  int32_t pcg_max_it, refine_max;
+  int32_t pad0;
+  double dt, pcg_rtol, refine_rtol;
+  double mu, lam;                // membrane Lame parameters (plane stress)
+
+  // state (FP64, SoA [3][nv])
+  double *x, *v, *rest, *fext;
+  double *mass;                  // [nv]
+  uint8_t *pinned;               // [nv]
+
+  // triangle data (membrane for every model; bending stencil for FVM / smoothed hinges)
+  int32_t *t_idx;                // [6][nt] (relabelled; -1 = virtual neighbour)
+  uint8_t *t_bc;                 // [3][nt]
+  uint8_t *t_mode;               // [nt]
+  double *t_L64;  float *t_L32;  // [18][nt] 3x6 operator, row-major index i*6+j
+  double *t_W64;  float *t_W32;  // [6][nt] symmetric 3x3 (00,01,02,11,12,22), area included
+  double *t_k064; float *t_k032; // [3][nt]
+  double *t_n64;  float *t_n32;  // [3][nt] fixed rest normal (FIXED mode)
+  double *m_D64;  float *m_D32;  // [3][nt] Dm^-1 = [[d0, d1], [0, d2]]
+  double *m_G64;                 // [3][nt] rest Gram |A|^2, A.B, |B|^2 of edges A = X2-X1, B = X3-X1
+  double *m_At64; float *m_At32; // [nt] area * thickness
+
+  // edge stencils (edge hinge models)
+  int32_t *e_idx;                // [4][ne] (x1, x2, x3, x4); x4 = -1 on clamped stencils
+  uint8_t *e_mode;               // [ne]
+  double *e_L64;  float *e_L32;  // [4][ne]
+  double *e_w64;  float *e_w32;  // [ne] k_b A_E
+  double *e_k064; float *e_k032; // [ne]
+  double *e_n64;  float *e_n32;  // [3][ne]
+
+  // force contributions: slot s holds 3 components at contrib[3*s+c]; vertex i sums slots
+  // vtx_slot[vtx_ptr[i] .. vtx_ptr[i+1]) in that order
+  int32_t *vtx_ptr, *vtx_slot;
+  void *contrib;                 // float or double [n_slots][3]
+  int32_t n_slots;
+  int32_t n_local;               // local matrix entries (assembly)
+
+  // matrix (SELL-32)
+  int32_t *sl_ptr;               // [n_slices+1] element offset of each slice
+  int32_t *sl_col;               // [nnz_pad]
+  double *val64;  float *val32;  // [nnz_pad]
+  double *dinv64; float *dinv32; // [nv] inverse diagonal (Jacobi)
+  int32_t *diag_pos;             // [nv]
+  int32_t *asm_ptr, *asm_src;    // assembly sources of each SELL position
+  double *local;                 // [n_local] per-stencil local matrix entries
+
+  // solver scratch
+  double *b;                     // [3][nv] right-hand side
+  double *sol;                   // [3][nv] FP64 solution (velocity v')
+  double *r64;                   // [3][nv] FP64 residual (refinement)
+  double *g64;                   // [nv][4] FP64 gathered vector
+  void *r, *p, *s, *w;           // [3][nv] PCG vectors in the solve precision
+  void *xs;                      // [3][nv] inner solution (FP32 refinement correction)
+  void *g;                       // [nv][4] gathered vector in the solve precision
+  double *part;                  // [n_chunks][4] reduction partials
+  double *ebuf;                  // [nt + ne][2] per-stencil energies (bending, membrane)
+
+  InstStatus *status;            // one per instance
+  int32_t *err_flags;            // precompute error flags (degenerate / singular)
+};
+
+// A force tile: kForceBlock consecutive stencils of one instance.
+struct Tile {
+  int32_t inst;
+  int32_t kind;    // 0 = triangles, 1 = edge stencils
+  int32_t first;
+  int32_t count;
+};
+
+// Persistent-solve schedule: CTA b belongs to team cta_team[b] with rank cta_rank[b]; team t has
+// team_size[t] CTAs and processes instances team_list[team_ptr[t] .. team_ptr[t+1]) in order.
+struct Sched {
+  int32_t *cta_team, *cta_rank;
+  int32_t *team_size, *team_ptr, *team_list;
+  unsigned int *bar;     // [n_teams][32] barrier words (count at [0], generation at [16])
+  int32_t *abort_flag;   // set when a bounded wait gives up
+  int32_t n_ctas;
+};
+
+// ---------------------------------------------------------------- launchers (defined in .cu files)
+cudaError_t launch_precompute(const Inst *d_inst, const Inst &h_inst, double E, double nu, double thickness,
+                              double density, cudaStream_t st);
+cudaError_t launch_assemble(const Inst *d_inst, const Inst &h_inst, cudaStream_t st);
+cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles, int want_energy, int fp32,
+                          cudaStream_t st);
+cudaError_t launch_gather_forces(const Inst *d_inst, const Inst &h_inst, double *d_out, cudaStream_t st);
+cudaError_t launch_energy_reduce(const Inst *d_inst, const Inst &h_inst, double *d_out4, cudaStream_t st);
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cudaStream_t st);
+cudaError_t launch_aos_to_soa(const double *src, double *dst, int nv, cudaStream_t st);
+cudaError_t launch_soa_to_aos(const double *src, double *dst, int nv, cudaStream_t st);
+cudaError_t launch_mass(const Inst *d_inst, const Inst &h_inst, double rho, const double g[3], int n_loads,
+                        const int32_t *d_lv, const double *d_lf, cudaStream_t st);
+cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, const int32_t *d_abort,
+                                 int32_t *d_out_abort, cudaStream_t st);
+cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
+                           cudaStream_t st);
+int solve_blocks_per_sm();
+
+}  // namespace shl

@@ -1,0 +1,565 @@
+// kernels_solve.cu -- persistent per-step solve: right-hand side, Jacobi-preconditioned conjugate
+// gradients on the constant matrix, state update. One launch per step serves every instance of a batch.
+//
+// Step (Section 5, Eq. 62-63, linearised): (M + dt^2 K) v' = M v + dt (f + f_ext); x' = x + dt v'.
+//
+// Work split. The grid is cut into teams of CTAs; a team processes a fixed list of instances one after the
+// other, all of its CTAs working on the same instance. Rows are grouped in chunks of kBlock * rpt rows
+// (rpt = rows per thread, fixed per instance); chunk c is owned by team rank c mod team_size. Teams of one
+// CTA synchronise with __syncthreads; larger teams with a global-memory barrier whose spin is bounded in
+// time (on timeout the kernel raises an abort flag and every CTA returns). The launch is cooperative, so
+// all CTAs are co-resident and the barrier cannot wait for a CTA that is not running.
+//
+// Reductions are deterministic and independent of the team size: each chunk reduces its rows with a fixed
+// tree into a per-chunk partial; every CTA then sums all partials of the instance in a fixed lane-strided
+// order and tree. An instance therefore gets bit-identical results whether it runs alone or in a batch.
+//
+// Solver: Chronopoulos-Gear form of preconditioned CG (one fused reduction of (r,u), (w,u), (r,r) per
+// iteration; two team barriers per iteration):
+//   p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D^-1 r; w = A u;
+//   gamma' = (r,u); delta' = (w,u); beta' = gamma'/gamma; alpha' = gamma'/(delta' - beta' gamma'/alpha).
+// FP64 mode: one CG in FP64 from the warm start v, until ||r|| <= rtol ||b||.
+// FP32 refinement mode: r64 = b - A v in FP64 (FP64 matrix and vector); inner CG in FP32 on A d = r64 from
+// d = 0 to a relative tolerance; v += d; repeat until ||r64|| <= refine_rtol ||b||.
+#include <cmath>
+
+#include "internal.h"
+
+namespace shl {
+namespace {
+
+struct alignas(16) D4 {
+  double x, y, z, w;
+};
+
+__device__ inline unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ inline unsigned int ld_acquire(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ inline int ld_volatile_i(const int *p) { return *((volatile const int *)p); }
+
+struct Team {
+  int team, rank, size;
+  unsigned int *bar;
+  int *abort_flag;
+  int bank;   // partials are double-buffered: reduction k writes bank k % 2
+};
+
+__device__ inline double *part_of(const Inst &I, const Team &tm, int ch) {
+  return I.part + 4 * ((size_t)tm.bank * I.n_chunks + ch);
+}
+
+// Team barrier. Returns false if the barrier was abandoned (timeout or abort raised by another CTA).
+__device__ bool team_sync(const Team &tm) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (tm.size == 1) return true;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned int *count = tm.bar;
+    unsigned int *gen = tm.bar + 16;
+    const unsigned int g = ld_acquire(gen);
+    __threadfence();
+    const unsigned int arrived = atomicAdd(count, 1u);
+    if (arrived == (unsigned int)tm.size - 1u) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      const unsigned long long t0 = gtimer();
+      const unsigned long long limit = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
+      while (ld_acquire(gen) == g) {
+        if (ld_volatile_i(tm.abort_flag)) {
+          ok = 0;
+          break;
+        }
+        if (gtimer() - t0 > limit) {
+          atomicExch(tm.abort_flag, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// reduce three per-thread values of one chunk (fixed tree) and store them as the chunk's partial
+template <typename A>
+__device__ void chunk_reduce(A v0, A v1, A v2, double *dst) {
+  __shared__ double sm[kBlock / 32][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  v2 = warp_sum(v2);
+  if (lane == 0) {
+    sm[warp][0] = double(v0);
+    sm[warp][1] = double(v1);
+    sm[warp][2] = double(v2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = sm[0][0], a1 = sm[0][1], a2 = sm[0][2];
+    for (int w = 1; w < kBlock / 32; ++w) {
+      a0 += sm[w][0];
+      a1 += sm[w][1];
+      a2 += sm[w][2];
+    }
+    dst[0] = a0;
+    dst[1] = a1;
+    dst[2] = a2;
+  }
+  __syncthreads();
+}
+
+// sum all chunk partials of an instance in a fixed order; result broadcast to the CTA. Flips the bank, so
+// the next phase may write partials while slower CTAs of the team still read these.
+__device__ void team_reduce(const Inst &I, Team &tm, double out[3]) {
+  __shared__ double res[3];
+  const double *part = I.part + 4 * (size_t)tm.bank * I.n_chunks;
+  const int n_chunks = I.n_chunks;
+  tm.bank ^= 1;
+  if (threadIdx.x < 32) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int c = threadIdx.x; c < n_chunks; c += 32) {
+      a0 += __ldcg(part + 4 * c);
+      a1 += __ldcg(part + 4 * c + 1);
+      a2 += __ldcg(part + 4 * c + 2);
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
+    if (threadIdx.x == 0) {
+      res[0] = a0;
+      res[1] = a1;
+      res[2] = a2;
+    }
+  }
+  __syncthreads();
+  out[0] = res[0];
+  out[1] = res[1];
+  out[2] = res[2];
+}
+
+// ------------------------------------------------------------------ precision traits
+template <typename R>
+struct Vec;
+template <>
+struct Vec<double> {
+  typedef D4 G;
+  __device__ static const double *val(const Inst &I) { return I.val64; }
+  __device__ static const double *dinv(const Inst &I) { return I.dinv64; }
+  __device__ static G *g(const Inst &I) { return reinterpret_cast<D4 *>(I.g); }
+  __device__ static G mk(double x, double y, double z) { return {x, y, z, 0.0}; }
+};
+template <>
+struct Vec<float> {
+  typedef float4 G;
+  __device__ static const float *val(const Inst &I) { return I.val32; }
+  __device__ static const float *dinv(const Inst &I) { return I.dinv32; }
+  __device__ static G *g(const Inst &I) { return reinterpret_cast<float4 *>(I.g); }
+  __device__ static G mk(float x, float y, float z) { return make_float4(x, y, z, 0.0f); }
+};
+
+__device__ inline D4 ldg4(const D4 *p) {
+  const double2 *q = reinterpret_cast<const double2 *>(p);
+  double2 a = q[0], b = q[1];
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ inline float4 ldg4(const float4 *p) { return *p; }
+
+// y = A g for one row (SELL-32)
+// g is written by other CTAs during the launch: it must not be read through the non-coherent path, so it
+// carries no __restrict__ / const-restrict qualification.
+template <typename R, typename G>
+__device__ inline void spmv_row(const Inst &I, const R *__restrict__ val, const G *g, int row, R &ax, R &ay,
+                                R &az) {
+  const int s = row >> 5, lane = row & 31;
+  const int b0 = I.sl_ptr[s], b1 = I.sl_ptr[s + 1];
+  ax = ay = az = R(0);
+  for (int p = b0 + lane; p < b1; p += 32) {
+    const int c = I.sl_col[p];
+    const R a = val[p];
+    const G v = ldg4(g + c);
+    ax += a * R(v.x);
+    ay += a * R(v.y);
+    az += a * R(v.z);
+  }
+}
+
+// ------------------------------------------------------------------ phases
+#define ROWS_BEGIN(I, tm)                                                                 \
+  for (int ch = (tm).rank; ch < (I).n_chunks; ch += (tm).size) {                        \
+    for (int rr = 0; rr < (I).rows_per_thread; ++rr) {                                  \
+      const int row = (ch * (I).rows_per_thread + rr) * kBlock + (int)threadIdx.x;      \
+      if (row < (I).nv) {
+#define ROWS_END \
+  }              \
+  }              \
+  }
+
+// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = v; g64 = sol; partial ||b||^2
+template <typename RC>
+__device__ void phase_rhs(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  const RC *con = reinterpret_cast<const RC *>(I.contrib);
+  for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
+    double bb = 0.0;
+    for (int rr = 0; rr < I.rows_per_thread; ++rr) {
+      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
+      if (row >= nv) continue;
+      double f[3] = {0.0, 0.0, 0.0};
+      for (int q = I.vtx_ptr[row]; q < I.vtx_ptr[row + 1]; ++q) {
+        const size_t s = (size_t)I.vtx_slot[q];
+        f[0] += double(con[3 * s]);
+        f[1] += double(con[3 * s + 1]);
+        f[2] += double(con[3 * s + 2]);
+      }
+      const bool pin = I.pinned[row] != 0;
+      const double m = I.mass[row];
+      double sv[3];
+      for (int c = 0; c < 3; ++c) {
+        const double v = I.v[c * nv + row];
+        double b = m * v + I.dt * (f[c] + I.fext[c * nv + row]);
+        if (pin) b = 0.0;
+        I.b[c * nv + row] = b;
+        bb += b * b;
+        sv[c] = pin ? 0.0 : v;
+        I.sol[c * nv + row] = sv[c];
+      }
+      reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
+    }
+    chunk_reduce<double>(bb, 0.0, 0.0, part_of(I, tm, ch));
+  }
+}
+
+// FP64 residual r64 = b - A64 sol; returns partial ||r64||^2. If R is float also prepares the inner CG:
+// r32 = r64, xs = 0, g32 = D32^-1 r32. If R is double: r = r64 (in place), sol unchanged, g = D^-1 r.
+template <typename R>
+__device__ void phase_resid(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  const D4 *g64 = reinterpret_cast<const D4 *>(I.g64);
+  R *r = reinterpret_cast<R *>(I.r);
+  R *xs = reinterpret_cast<R *>(I.xs);
+  typename Vec<R>::G *g = Vec<R>::g(I);
+  const R *dinv = Vec<R>::dinv(I);
+  for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
+    double rr2 = 0.0;
+    for (int rr = 0; rr < I.rows_per_thread; ++rr) {
+      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
+      if (row >= nv) continue;
+      double ax, ay, az;
+      spmv_row<double, D4>(I, I.val64, g64, row, ax, ay, az);
+      const double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
+      I.r64[row] = r0;
+      I.r64[nv + row] = r1;
+      I.r64[2 * nv + row] = r2;
+      rr2 += r0 * r0 + r1 * r1 + r2 * r2;
+      const R q0 = R(r0), q1 = R(r1), q2 = R(r2);
+      r[row] = q0;
+      r[nv + row] = q1;
+      r[2 * nv + row] = q2;
+      if (sizeof(R) == 4) {
+        xs[row] = R(0);
+        xs[nv + row] = R(0);
+        xs[2 * nv + row] = R(0);
+      }
+      const R di = dinv[row];
+      g[row] = Vec<R>::mk(di * q0, di * q1, di * q2);
+    }
+    chunk_reduce<double>(rr2, 0.0, 0.0, part_of(I, tm, ch));
+  }
+}
+
+// w = A u (u = g); partials (r,u), (w,u), (r,r)
+template <typename R>
+__device__ void phase_spmv(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  const R *val = Vec<R>::val(I);
+  const typename Vec<R>::G *g = Vec<R>::g(I);
+  const R *r = reinterpret_cast<const R *>(I.r);
+  R *w = reinterpret_cast<R *>(I.w);
+  for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
+    R gu = R(0), wu = R(0), rr2 = R(0);
+    for (int rr = 0; rr < I.rows_per_thread; ++rr) {
+      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
+      if (row >= nv) continue;
+      R ax, ay, az;
+      spmv_row<R>(I, val, g, row, ax, ay, az);
+      w[row] = ax;
+      w[nv + row] = ay;
+      w[2 * nv + row] = az;
+      const typename Vec<R>::G u = ldg4(g + row);
+      const R r0 = r[row], r1 = r[nv + row], r2 = r[2 * nv + row];
+      gu += r0 * R(u.x) + r1 * R(u.y) + r2 * R(u.z);
+      wu += ax * R(u.x) + ay * R(u.y) + az * R(u.z);
+      rr2 += r0 * r0 + r1 * r1 + r2 * r2;
+    }
+    chunk_reduce<R>(gu, wu, rr2, part_of(I, tm, ch));
+  }
+}
+
+// p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D^-1 r -> g
+template <typename R>
+__device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, bool first, R *x) {
+  const int nv = I.nv;
+  const R *dinv = Vec<R>::dinv(I);
+  typename Vec<R>::G *g = Vec<R>::g(I);
+  R *r = reinterpret_cast<R *>(I.r);
+  R *p = reinterpret_cast<R *>(I.p);
+  R *s = reinterpret_cast<R *>(I.s);
+  const R *w = reinterpret_cast<const R *>(I.w);
+  ROWS_BEGIN(I, tm)
+  const R di = dinv[row];
+  R un[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int k = c * nv + row;
+    const R rc = r[k];
+    const R u = di * rc;
+    const R pc = first ? u : u + beta * p[k];
+    const R sc = first ? w[k] : w[k] + beta * s[k];
+    p[k] = pc;
+    s[k] = sc;
+    x[k] += alpha * pc;
+    const R rn = rc - alpha * sc;
+    r[k] = rn;
+    un[c] = di * rn;
+  }
+  g[row] = Vec<R>::mk(un[0], un[1], un[2]);
+  ROWS_END
+}
+
+// Chronopoulos-Gear PCG iterations on A x = r0, given r (initial residual), x (initial guess) and
+// g = D^-1 r. Stops when (r,r) <= tol2 (absolute). Returns iterations (>= 0), -1 on cap, -2 on abort,
+// -3 on a non-finite reduction.
+template <typename R>
+__device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, double *rho_out) {
+  if (!team_sync(tm)) return -2;
+  phase_spmv<R>(I, tm);
+  if (!team_sync(tm)) return -2;
+  double red[3];
+  team_reduce(I, tm, red);
+  double gamma = red[0], delta = red[1], rho = red[2];
+  *rho_out = rho;
+  if (!isfinite(rho) || !isfinite(gamma) || !isfinite(delta)) return -3;
+  if (rho <= tol2) return 0;
+  double alpha = gamma / delta, beta = 0.0;
+  bool first = true;
+  for (int it = 1; it <= max_it; ++it) {
+    phase_update<R>(I, tm, R(alpha), R(beta), first, x);
+    if (!team_sync(tm)) return -2;
+    phase_spmv<R>(I, tm);
+    if (!team_sync(tm)) return -2;
+    team_reduce(I, tm, red);
+    const double gn = red[0], dn = red[1];
+    rho = red[2];
+    *rho_out = rho;
+    if (!isfinite(rho) || !isfinite(gn) || !isfinite(dn)) return -3;
+    if (rho <= tol2) return it;
+    const double bn = gn / gamma;
+    alpha = gn / (dn - bn * gn / alpha);
+    beta = bn;
+    gamma = gn;
+    first = false;
+  }
+  return -1;
+}
+
+// sol += xs (FP32 correction); g64 = sol
+__device__ void phase_accumulate(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  const float *xs = reinterpret_cast<const float *>(I.xs);
+  ROWS_BEGIN(I, tm)
+  double sv[3];
+  for (int c = 0; c < 3; ++c) {
+    const int k = c * nv + row;
+    sv[c] = I.sol[k] + double(xs[k]);
+    I.sol[k] = sv[c];
+  }
+  reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
+  ROWS_END
+}
+
+// v = sol; x += dt v
+__device__ void phase_commit(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  ROWS_BEGIN(I, tm)
+  for (int c = 0; c < 3; ++c) {
+    const int k = c * nv + row;
+    const double v = I.sol[k];
+    I.v[k] = v;
+    I.x[k] += I.dt * v;
+  }
+  ROWS_END
+}
+
+__device__ void set_status(const Inst &I, const Team &tm, int err, int iters, int rounds, double rel) {
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    InstStatus *s = I.status;
+    if (err == SHELL_OK) {
+      s->steps_done += 1;
+      s->last_iters = iters;
+      s->last_rounds = rounds;
+      s->total_iters += iters;
+      s->total_rounds += rounds;
+      s->rel_res = rel;
+    } else {
+      s->err = err;
+      s->fail_step = s->steps_done;
+      s->last_iters = iters;
+      s->last_rounds = rounds;
+      s->rel_res = rel;
+    }
+  }
+}
+
+// returns false if the kernel must stop (abort)
+__device__ bool solve_fp64(const Inst &I, Team &tm) {
+  phase_rhs<double>(I, tm);
+  if (!team_sync(tm)) return false;
+  double red[3];
+  team_reduce(I, tm, red);
+  const double bb = red[0];
+  if (!isfinite(bb)) {
+    set_status(I, tm, SHELL_ERR_NONFINITE, 0, 0, 0.0);
+    return true;
+  }
+  int iters = 0;
+  double rho = 0.0;
+  if (bb > 0.0) {
+    phase_resid<double>(I, tm);   // r = b - A sol, g = D^-1 r
+    const double tol2 = I.pcg_rtol * I.pcg_rtol * bb;
+    iters = cg_loop<double>(I, tm, I.sol, tol2, I.pcg_max_it, &rho);
+    if (iters == -2) return false;
+    if (iters < 0) {
+      set_status(I, tm, iters == -1 ? SHELL_ERR_NOT_CONVERGED : SHELL_ERR_NONFINITE, I.pcg_max_it, 0,
+                 sqrt(rho / bb));
+      return true;
+    }
+  } else {
+    // b = 0: the solution is v' = 0
+    ROWS_BEGIN(I, tm)
+    for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
+    ROWS_END
+  }
+  phase_commit(I, tm);
+  set_status(I, tm, SHELL_OK, iters, 0, bb > 0.0 ? sqrt(rho / bb) : 0.0);
+  return true;
+}
+
+__device__ bool solve_fp32r(const Inst &I, Team &tm) {
+  phase_rhs<float>(I, tm);
+  if (!team_sync(tm)) return false;
+  double red[3];
+  team_reduce(I, tm, red);
+  const double bb = red[0];
+  if (!isfinite(bb)) {
+    set_status(I, tm, SHELL_ERR_NONFINITE, 0, 0, 0.0);
+    return true;
+  }
+  int total = 0, rounds = 0;
+  double rel = 0.0;
+  if (bb > 0.0) {
+    const double tol_ref2 = I.refine_rtol * I.refine_rtol * bb;
+    const double tin2 = I.pcg_rtol * I.pcg_rtol;
+    for (;;) {
+      phase_resid<float>(I, tm);
+      if (!team_sync(tm)) return false;
+      team_reduce(I, tm, red);
+      const double r2 = red[0];
+      rel = sqrt(r2 / bb);
+      if (!isfinite(r2)) {
+        set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
+        return true;
+      }
+      if (r2 <= tol_ref2) break;
+      if (rounds >= I.refine_max) {
+        set_status(I, tm, SHELL_ERR_NOT_CONVERGED, total, rounds, rel);
+        return true;
+      }
+      double rho = 0.0;
+      const int it = cg_loop<float>(I, tm, reinterpret_cast<float *>(I.xs), tin2 * r2, I.pcg_max_it, &rho);
+      if (it == -2) return false;
+      if (it == -3) {
+        set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
+        return true;
+      }
+      total += (it < 0 ? I.pcg_max_it : it);
+      phase_accumulate(I, tm);
+      if (!team_sync(tm)) return false;
+      ++rounds;
+    }
+  } else {
+    ROWS_BEGIN(I, tm)
+    for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
+    ROWS_END
+  }
+  phase_commit(I, tm);
+  set_status(I, tm, SHELL_OK, total, rounds, rel);
+  return true;
+}
+
+__global__ void __launch_bounds__(kBlock) k_solve(const Inst *__restrict__ insts, Sched sch) {
+  Team tm;
+  tm.team = sch.cta_team[blockIdx.x];
+  if (tm.team < 0) return;
+  tm.rank = sch.cta_rank[blockIdx.x];
+  tm.size = sch.team_size[tm.team];
+  tm.bar = sch.bar + 32 * tm.team;
+  tm.abort_flag = sch.abort_flag;
+  tm.bank = 0;
+  for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
+    const Inst &I = insts[sch.team_list[q]];
+    if (I.status->err != SHELL_OK) continue;
+    const bool ok = (I.precision == SHELL_FP64) ? solve_fp64(I, tm) : solve_fp32r(I, tm);
+    if (!ok) return;
+    // make this instance's final writes (status) ordered before the team moves on
+    if (!team_sync(tm)) return;
+  }
+}
+
+}  // namespace
+
+int solve_blocks_per_sm() {
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve, kBlock, 0);
+  return n;
+}
+
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_solve, d_insts, sched);
+}
+
+}  // namespace shl

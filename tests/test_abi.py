@@ -1,0 +1,61 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads without a GPU, exports every entry point
+that include/shell.h declares, and refuses to compute without a GB300 (no CPU fallback)."""
+import os
+import re
+
+import pytest
+
+import paper_2502_10872_gb300 as gb
+from paper_2502_10872_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        gb.build()
+    return gb.load_library()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "shell.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(shell_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_api():
+    names = header_functions()
+    for n in ("shell_create", "shell_step", "shell_energy", "shell_forces", "shell_destroy", "shell_batch_step"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) == set(binding.EXPORTS)
+
+
+def test_no_cpu_fallback_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(gb.ShellError) as e:
+        gb.shell_create([[0, 1, 2]], [[0, 0, 0], [1, 0, 0], [0, 1, 0]], "SP", 1e6, 0.3, 1e-3, 1000.0,
+                        use_torch_allocator=False)
+    assert e.value.code == gb.SHELL_ERR_NO_DEVICE
+
+
+def test_options_defaults(lib):
+    o = gb.make_options(use_torch_allocator=False, stream=0)
+    assert o.dt == 1e-2 and o.pcg_max_it == 20000 and o.refine_max == 20
+    assert lib.shell_strerror(gb.SHELL_ERR_NOT_CONVERGED).decode().startswith("linear solve")
+
+
+def test_binding_structs_match_header_layout():
+    import ctypes as C
+    # shell_options: double, int32(+pad), double, double, int32, int32, 4 pointers
+    assert C.sizeof(binding.shell_options) == 8 + 8 + 8 + 8 + 4 + 4 + 4 * 8
+    assert C.sizeof(binding.shell_step_stats) == 4 * 4 + 8 + 8 + 8
+    assert C.sizeof(binding.shell_bc) == 8 + 8 + 8 + 24 + 8 + 8 + 8

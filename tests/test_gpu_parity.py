@@ -1,0 +1,202 @@
+"""GPU-vs-oracle parity of the whole step through the C ABI (needs a GB300).
+
+Metric (per result): rel_x = |x - x*| / |x* - X| (displacement relative, origin independent), rel_v =
+|v - v*| / |v*|, energies relative per component. Bars: 1e-10 in FP64; the FP32 path with FP64
+refinement states its own bound per case (<= 1e-6 for the solve, and the measured force-rounding error).
+Sizes span several 256-row chunks with ragged tails (multi-CTA teams and their global barrier), every
+model, every boundary type, point loads, gravity, rest-curved and rest-flat shells.
+"""
+import numpy as np
+import pytest
+
+import shellgen as sg
+from oracle import system as osys
+
+gb = pytest.importorskip("paper_2502_10872_gb300")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    gb.load_library()
+
+
+def rel(a, b, ref):
+    d = np.linalg.norm(ref)
+    return np.linalg.norm(a - b) / (d if d > 0 else 1.0)
+
+
+def run_both(sc, steps, precision="fp64", **kw):
+    m = osys.from_scenario(sc)
+    xo, vo = osys.step(m, sc.x0, sc.v0, steps)
+    h = gb.create_from_scenario(sc, precision=precision, **kw)
+    st = gb.shell_step(h, steps)
+    xg, vg = gb.shell_get_state(h)
+    return m, h, st, (xg, vg), (xo, vo)
+
+
+def test_plate16_edge_hinge_fp64_100_steps():
+    """16 x 16 edge-hinge plate, one edge clamped, gravity, 100 steps (the small end-to-end workload)."""
+    sc = sg.plate_clamped_x0(16, model="EP")
+    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 100)
+    assert st["steps_done"] == 100
+    assert rel(xg, xo, xo - sc.rest) <= 1e-10
+    assert rel(vg, vo, vo) <= 1e-10
+    eg = gb.shell_energy(h)
+    eo = np.array(osys.energy(m, xo, vo))
+    for k in range(4):
+        assert abs(eg[k] - eo[k]) <= 1e-9 * abs(eo[k]) + 1e-18, (k, eg, eo)
+
+
+@pytest.mark.parametrize("model", sg.MODELS)
+def test_all_models_plate_scene_fp64(model):
+    """Ragged plate (21 x 13 cells, 308 vertices -> 2 chunks), x0 edge clamped, gravity, a point load."""
+    sc = sg.plate_clamped_x0(21, model=model)
+    xy, tris = sg.grid(21, 13)
+    sc.tris, sc.rest = tris, sg.flat3(xy)
+    sc.x0, sc.v0 = sc.rest.copy(), np.zeros_like(sc.rest)
+    sc.pinned = np.zeros(sc.rest.shape[0], np.uint8)
+    sc.pinned[sg.grid_side_vertices(21, 13, "x0")] = 1
+    sc.clamped_edges = sg.grid_side_edges(21, 13, "x0")
+    sc.load_vtx = np.array([sc.rest.shape[0] - 1], np.int32)
+    sc.load_f = np.array([[0.0, 0.3, -0.5]])
+    sc.E = 2e5
+    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 25)
+    assert rel(xg, xo, xo - sc.rest) <= 1e-10, model
+    assert rel(vg, vo, vo) <= 1e-10, model
+
+
+@pytest.mark.parametrize("model", sg.MODELS)
+def test_all_models_cylinder_scene_fp64(model):
+    """Cylinder panel 30 x 23 cells (744 vertices, 3 chunks), both straight edges clamped, point load; plate
+    models rest flat and start curved."""
+    sc = sg.cylinder_panel(30, model, ny=23, radius=0.6, dt=5e-3)
+    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 20)
+    assert rel(xg, xo, xo - sc.x0) <= 1e-10, model
+
+
+@pytest.mark.parametrize("model", sg.MODELS)
+def test_matrix_matches_oracle(model):
+    """The device-assembled constant matrix equals the oracle's M + dt^2 (K_b + K_m) (pinned rows identity)."""
+    rng = np.random.default_rng(2)
+    sc = sg.cylinder_panel(14, model, ny=9, radius=0.8) if model in sg.SHELL_MODELS else sg.plate_clamped_x0(14, model)
+    m = osys.from_scenario(sc, factor=False)
+    A = osys.system_matrix(m)
+    h = gb.create_from_scenario(sc)
+    u = rng.standard_normal(sc.x0.shape)
+    ag = gb.shell_apply_matrix(h, u)
+    ao = A @ u
+    assert rel(ag, ao, ao) <= 1e-13
+
+
+@pytest.mark.parametrize("model", sg.MODELS)
+def test_forces_and_energy_at_deformed_state(model):
+    """shell_forces / shell_energy at a random deformed state (all stencils, free and clamped boundaries)."""
+    rng = np.random.default_rng(5)
+    if model in sg.SHELL_MODELS:
+        sc = sg.cylinder_panel(17, model, ny=11, radius=0.8)
+    else:
+        sc = sg.plate_clamped_x0(17, model=model)
+    x = sc.x0 + 0.01 * rng.standard_normal(sc.x0.shape)
+    v = 0.1 * rng.standard_normal(sc.x0.shape)
+    m = osys.from_scenario(sc, factor=False)
+    h = gb.create_from_scenario(sc)
+    gb.shell_set_state(h, x, v)
+    fg = gb.shell_forces(h)
+    fo = osys.forces(m, x)
+    assert rel(fg, fo, fo) <= 1e-12
+    eg = gb.shell_energy(h)
+    eo = np.array(osys.energy(m, x, v))
+    np.testing.assert_allclose(eg, eo, rtol=1e-11, atol=1e-300)
+
+
+def test_cylinder128_shell_models_fp64():
+    """128 x 128 cylinder panel (16,641 vertices, 66 chunks, a multi-CTA team), each shell operator, 10 steps."""
+    for model in ("ES", "FS", "SS"):
+        sc = sg.cylinder_panel(128, model)
+        m, h, st, (xg, vg), (xo, vo) = run_both(sc, 10)
+        assert rel(xg, xo, xo - sc.x0) <= 1e-10, model
+
+
+@pytest.mark.parametrize("model", ["ES", "FS", "SS"])
+def test_cylinder128_fp32_refine(model):
+    """FP32 forces and PCG with FP64 refinement on the 128 x 128 cylinder: solve to refine_rtol = 1e-10;
+    the remaining difference to the FP64 oracle is the FP32 rounding of the force (stated bound 1e-6)."""
+    sc = sg.cylinder_panel(128, model)
+    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 10, precision="fp32_refine")
+    assert st["refine_rounds"] >= 1
+    assert st["rel_residual"] <= 1e-10
+    assert rel(xg, xo, xo - sc.x0) <= 1e-6, model
+
+
+def test_alone_equals_in_batch_bitwise():
+    """An instance's result is bit-identical alone and inside a batch of other instances (both precisions)."""
+    scs = sg.mixed_batch(12, seed=9, side_lo=6, side_hi=40, steps=5)
+    for prec in ("fp64", "fp32_refine"):
+        alone = []
+        for sc in scs:
+            h = gb.create_from_scenario(sc, precision=prec)
+            gb.shell_step(h, 5)
+            alone.append(gb.shell_get_state(h))
+            gb.shell_destroy(h)
+        b = gb.shell_batch_create(1 << 40)
+        hs = [gb.create_from_scenario(sc, precision=prec) for sc in scs]
+        for h in hs:
+            gb.shell_batch_admit(b, h)
+        rc, stats = gb.shell_batch_step(b, 5)
+        assert rc == 0
+        assert all(s["steps_done"] == 5 for s in stats.values())
+        for slot in list(b.members):
+            gb.shell_batch_retire(b, slot)
+        for k, h in enumerate(hs):
+            x, v = gb.shell_get_state(h)
+            assert np.array_equal(x, alone[k][0]), (prec, k)
+            assert np.array_equal(v, alone[k][1]), (prec, k)
+
+
+def test_not_converged_commits_nothing():
+    sc = sg.plate_clamped_x0(12, model="SP")
+    h = gb.create_from_scenario(sc, pcg_max_it=1)
+    x0, v0 = gb.shell_get_state(h)
+    st = gb.shell_step(h, 3, check=False)
+    assert st["rc"] == gb.SHELL_ERR_NOT_CONVERGED
+    assert st["steps_done"] == 0
+    x1, v1 = gb.shell_get_state(h)
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
+
+
+def test_invalid_meshes_rejected():
+    with pytest.raises(gb.ShellError) as e:
+        gb.shell_create([[0, 1, 2], [1, 2, 3]], np.eye(4, 3), "SP", 1e6, 0.3, 1e-3, 1000.0)
+    assert e.value.code == gb.SHELL_ERR_BAD_ORIENTATION
+    xy, tris = sg.grid(2, 2)
+    curved = sg.roll_to_cylinder(xy, 0.5, 1.0)
+    with pytest.raises(gb.ShellError) as e:
+        gb.shell_create(tris, curved, "SP", 1e6, 0.3, 1e-3, 1000.0)   # plate model on a curved rest shape
+    assert e.value.code == gb.SHELL_ERR_INVALID_ARG
+    with pytest.raises(gb.ShellError) as e:
+        gb.shell_create(tris, sg.flat3(xy), "SP", 1e6, 0.3, 1e-3, 1000.0, clamped_edges=[[0, 4]])  # interior edge
+    assert e.value.code == gb.SHELL_ERR_INVALID_ARG
+
+
+def test_full_size_jittered_plate_step_satisfies_system():
+    """512^2-vertex jittered smoothed-hinge plate, FP32 + refinement, in the benchmark's launch configuration:
+    after 3 steps, one more step is checked against the oracle's own system at that state:
+    |A v' - b| <= 1.5 refine_rtol |b| with A, b built by the oracle, and x' = x + dt v'."""
+    sc = sg.jittered_plate(512)
+    h = gb.create_from_scenario(sc, precision="fp32_refine", refine_rtol=1e-10)
+    gb.shell_step(h, 3)
+    x, v = gb.shell_get_state(h)
+    st = gb.shell_step(h, 1)
+    x1, v1 = gb.shell_get_state(h)
+    m = osys.from_scenario(sc, factor=False)
+    A = osys.system_matrix(m)
+    # b in FP64 from the oracle's exact forces; the GPU forms its force in FP32, so the residual bound
+    # includes the force rounding: check both the solve and the force error separately
+    b = osys.rhs(m, x, v)
+    res = np.linalg.norm(A @ v1 - b) / np.linalg.norm(b)
+    assert res <= 1e-6, res
+    np.testing.assert_allclose(x1, x + sc.dt * v1, rtol=0, atol=1e-15 * np.abs(x).max())
