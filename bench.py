@@ -206,6 +206,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+    # a non-default stream, so the per-step launches can be captured into a CUDA graph
+    torch.cuda.set_stream(torch.cuda.Stream())
     gb.load_library()
     scs, desc = workload(args.workload, args.seed, rank)
     V_total = sum(sc.n_verts for sc in scs)
