@@ -170,7 +170,8 @@ def test_not_converged_commits_nothing():
 
 def test_invalid_meshes_rejected():
     with pytest.raises(gb.ShellError) as e:
-        gb.shell_create([[0, 1, 2], [1, 2, 3]], np.eye(4, 3), "SP", 1e6, 0.3, 1e-3, 1000.0)
+        gb.shell_create([[0, 1, 2], [1, 2, 3]], [[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], "SP", 1e6, 0.3,
+                        1e-3, 1000.0)
     assert e.value.code == gb.SHELL_ERR_BAD_ORIENTATION
     xy, tris = sg.grid(2, 2)
     curved = sg.roll_to_cylinder(xy, 0.5, 1.0)
