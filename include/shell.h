@@ -56,6 +56,7 @@ extern "C" {
 #define SHELL_ERR_CUDA -11            /* a CUDA runtime call failed */
 #define SHELL_ERR_NO_DEVICE -12       /* no CUDA device of compute capability 10.3 is available */
 #define SHELL_ERR_BUSY -13            /* the handle belongs to a batch and must be stepped through it */
+#define SHELL_ERR_STATIC_LIMIT -14    /* the request needs more than shell_step_noalloc's static scratch */
 
 /* ------------------------------------------------------------------------------------------ enums */
 /* Bending model (Section 4.2): E/F/S = edge-based / FVM / smoothed hinge, P/S = plate / shell. */
@@ -152,6 +153,23 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
  * refinement), x += dt v'. A step that fails (NOT_CONVERGED, NONFINITE, TIMEOUT) is not committed and
  * ends the call; the steps before it are committed. stats may be NULL. */
 int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
+
+/* The same steps as shell_step, for callers that cannot allocate device memory once their handles exist:
+ * for example a real-time loop whose device allocator is frozen after set-up, or a host framework that owns
+ * the whole device-memory budget and forbids allocation inside its step callback. shell_step's first call
+ * (and its first call after a batch retires the handle) allocates scheduling tables; this entry point never
+ * allocates: its launch scratch (team schedule, barrier words, abort flag, status read-back) is a
+ * file-scope static __device__ array of about 17 KB that every GPU loading the library holds until exit.
+ * The paper has no counterpart to this; it is a deployment variant of shell_step.
+ *   - Same arguments and results as shell_step (bit-identical states).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current; make that first call before any stream capture.
+ *   - The array is shared by every call in the process and keeps the last call's contents; the call clears
+ *     the words that must start at zero. Calls that overlap on the GPU (other streams or threads) race on
+ *     it: serialise them.
+ *   - Limit: one team of at most 2048 CTAs (an instance may use up to 2048 x 256 rows per chunk pass);
+ *     beyond that it returns SHELL_ERR_STATIC_LIMIT. */
+int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
 
 /* Energies at the current state, FP64: out[0] membrane, out[1] bending, out[2] kinetic 1/2 v^T M v,
  * out[3] external potential -sum f_ext . (x - X). */

@@ -24,7 +24,7 @@ ERRORS = {
     -1: "SHELL_ERR_INVALID_ARG", -2: "SHELL_ERR_NON_MANIFOLD", -3: "SHELL_ERR_BAD_ORIENTATION",
     -4: "SHELL_ERR_DEGENERATE", -5: "SHELL_ERR_SINGULAR_OPERATOR", -6: "SHELL_ERR_OOM", -7: "SHELL_ERR_BUDGET",
     -8: "SHELL_ERR_NOT_CONVERGED", -9: "SHELL_ERR_NONFINITE", -10: "SHELL_ERR_TIMEOUT", -11: "SHELL_ERR_CUDA",
-    -12: "SHELL_ERR_NO_DEVICE", -13: "SHELL_ERR_BUSY",
+    -12: "SHELL_ERR_NO_DEVICE", -13: "SHELL_ERR_BUSY", -14: "SHELL_ERR_STATIC_LIMIT",
 }
 for _c, _n in ERRORS.items():
     globals()[_n] = _c
@@ -33,7 +33,8 @@ PRECISIONS = {"fp64": 0, "fp32_refine": 1}
 
 # symbols declared in include/shell.h
 EXPORTS = (
-    "shell_default_options", "shell_strerror", "shell_create", "shell_step", "shell_energy", "shell_forces",
+    "shell_default_options", "shell_strerror", "shell_create", "shell_step", "shell_step_noalloc", "shell_energy",
+    "shell_forces",
     "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
@@ -106,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "shell_create": (C.c_int, [C.POINTER(shell_mesh), C.POINTER(shell_material), C.c_int32, C.POINTER(shell_bc),
                                    C.POINTER(shell_options), C.POINTER(P)]),
         "shell_step": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
+        "shell_step_noalloc": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
         "shell_energy": (C.c_int, [P, P]),
         "shell_forces": (C.c_int, [P, P]),
         "shell_apply_matrix": (C.c_int, [P, P, P]),
@@ -281,6 +283,17 @@ def shell_step(h: Handle, n_steps: int = 1, check: bool = True) -> dict:
     rc = load_library().shell_step(h.ptr, int(n_steps), C.byref(st))
     if check:
         _check(rc, "shell_step")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def shell_step_noalloc(h: Handle, n_steps: int = 1, check: bool = True) -> dict:
+    """shell_step that allocates no device memory (static launch scratch; see include/shell.h)."""
+    st = shell_step_stats()
+    rc = load_library().shell_step_noalloc(h.ptr, int(n_steps), C.byref(st))
+    if check:
+        _check(rc, "shell_step_noalloc")
     d = st.as_dict()
     d["rc"] = rc
     return d

@@ -537,6 +537,7 @@ const char *shell_strerror(int code) {
     case SHELL_ERR_CUDA: return cudaGetErrorString(last_cuda_error());
     case SHELL_ERR_NO_DEVICE: return "no CUDA device of compute capability 10.3";
     case SHELL_ERR_BUSY: return "handle is resident in a batch";
+    case SHELL_ERR_STATIC_LIMIT: return "request exceeds the static scratch of shell_step_noalloc (2048 CTAs)";
     default: return "unknown error";
   }
 }
@@ -805,6 +806,35 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
   if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
   return batch_step(h->solo, n_steps, stats);
+}
+
+// shell_step for callers that cannot allocate: the launch scratch is the static array of kernels_solve.cu
+int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
+  if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
+  if (h->batch) return SHELL_ERR_BUSY;
+  int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(), h->h.n_chunks));
+  if (team > static_max_ctas()) return SHELL_ERR_STATIC_LIMIT;
+  const InstStatus before = h->last_status;
+  InstStatus after{};
+  int32_t aborted = 0;
+  cudaError_t e = launch_step_static(h->d_inst, h->d_tiles, (int)h->tiles.size(), h->h.precision != SHELL_FP64, team,
+                                     n_steps, &after, &aborted, h->mem.st);
+  if (e != cudaSuccess) {
+    last_cuda_error() = e;
+    return SHELL_ERR_CUDA;
+  }
+  h->last_status = after;
+  if (stats) {
+    stats->steps_done = after.steps_done - before.steps_done;
+    stats->pcg_iterations = after.last_iters;
+    stats->refine_rounds = after.last_rounds;
+    stats->status = after.err;
+    stats->total_pcg_iterations = after.total_iters - before.total_iters;
+    stats->rel_residual = after.rel_res;
+    stats->total_refine_rounds = after.total_rounds - before.total_rounds;
+  }
+  if (aborted) return SHELL_ERR_TIMEOUT;
+  return after.err;
 }
 
 static int run_forces64(shell_handle *h, int want_energy) {

@@ -145,5 +145,8 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
 cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
                            cudaStream_t st);
 int solve_blocks_per_sm();
+int static_max_ctas();
+cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
+                               int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st);
 
 }  // namespace shl

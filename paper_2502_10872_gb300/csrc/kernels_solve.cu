@@ -562,4 +562,89 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cuda
   return cudaLaunchKernelEx(&cfg, k_solve, d_insts, sched);
 }
 
+// ---------------------------------------------------------------- step without device allocation
+// The launch scratch of the persistent solve (team schedule, barrier words, abort flag, status read-back)
+// for callers that cannot allocate device memory: it lives in this file-scope array, which every GPU that
+// loads the library holds until the process exits. Layout (32-bit words): [0, kStaticMaxCtas) team of each
+// CTA, [kStaticMaxCtas, 2 kStaticMaxCtas) rank, then team_size[1], team_ptr[2], team_list[1], the barrier
+// words (32), the abort flag, its read-back copy, and one InstStatus.
+constexpr int kStaticMaxCtas = 2048;
+constexpr int kStaticWords = 2 * kStaticMaxCtas + 4 + 32 + 2 + 64;
+static __device__ __align__(256) unsigned int g_static_scratch[kStaticWords];
+
+namespace {
+constexpr int kMaxDevices = 64;
+unsigned int *g_static_addr[kMaxDevices];   // device address of g_static_scratch, per device
+}  // namespace
+
+cudaError_t static_scratch_setup(unsigned int **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = reinterpret_cast<unsigned int *>(p);
+  }
+  *out = g_static_addr[dev];
+  return cudaSuccess;
+}
+
+int static_max_ctas() { return kStaticMaxCtas; }
+
+cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
+                               int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st) {
+  unsigned int *base = nullptr;
+  cudaError_t e = static_scratch_setup(&base);
+  if (e != cudaSuccess) return e;
+  if (team_ctas < 1 || team_ctas > kStaticMaxCtas) return cudaErrorInvalidValue;
+  // schedule: one team of team_ctas CTAs working on instance 0
+  int32_t *w = reinterpret_cast<int32_t *>(base);
+  Sched sc;
+  sc.cta_team = w;
+  sc.cta_rank = w + kStaticMaxCtas;
+  sc.team_size = w + 2 * kStaticMaxCtas;
+  sc.team_ptr = w + 2 * kStaticMaxCtas + 1;
+  sc.team_list = w + 2 * kStaticMaxCtas + 3;
+  sc.bar = base + 2 * kStaticMaxCtas + 4;
+  sc.abort_flag = w + 2 * kStaticMaxCtas + 4 + 32;
+  int32_t *abort_out = sc.abort_flag + 1;
+  InstStatus *status_out = reinterpret_cast<InstStatus *>(base + 2 * kStaticMaxCtas + 4 + 32 + 2 + 2);
+  sc.n_ctas = team_ctas;
+  static thread_local int32_t host_tab[2 * kStaticMaxCtas + 4];
+  for (int c = 0; c < team_ctas; ++c) {
+    host_tab[c] = 0;
+    host_tab[kStaticMaxCtas + c] = c;
+  }
+  host_tab[2 * kStaticMaxCtas] = team_ctas;
+  host_tab[2 * kStaticMaxCtas + 1] = 0;
+  host_tab[2 * kStaticMaxCtas + 2] = 1;
+  host_tab[2 * kStaticMaxCtas + 3] = 0;
+  if ((e = cudaMemcpyAsync(sc.cta_team, host_tab, 4 * team_ctas, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(sc.cta_rank, host_tab + kStaticMaxCtas, 4 * team_ctas, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(sc.team_size, host_tab + 2 * kStaticMaxCtas, 16, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  // the barrier words and the abort flag must start at zero; the array keeps the previous call's contents
+  if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (32 + 2), st)) != cudaSuccess) return e;
+  for (int k = 0; k < n_steps; ++k) {
+    if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st)) != cudaSuccess) return e;
+    if ((e = launch_solve(d_inst, sc, team_ctas, st)) != cudaSuccess) return e;
+  }
+  if ((e = launch_gather_status(d_inst, 1, status_out, sc.abort_flag, abort_out, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(h_status, status_out, sizeof(InstStatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(h_aborted, abort_out, sizeof(int32_t), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && *h_aborted) {
+    cudaMemsetAsync(sc.bar, 0, 4 * (32 + 2), st);
+    e = cudaStreamSynchronize(st);
+  }
+  return e;
+}
+
 }  // namespace shl
