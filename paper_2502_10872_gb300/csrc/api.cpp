@@ -104,6 +104,7 @@ struct shell_handle {
   std::vector<Tile> tiles;       // force tiles of this instance (inst index filled by the batch)
   Tile *d_tiles = nullptr;       // the same tiles on the device (inst index 0 = d_inst)
   double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
+  double sched_est = 64.0;       // estimate the current schedule was planned with
   int64_t nnz = 0, nnz_pad = 0;
   InstStatus last_status{};
 };
@@ -123,6 +124,7 @@ struct shell_batch {
   int n_tiles64 = 0, n_tiles32 = 0;
   Sched sched{};
   int grid = 0;
+  int prec = 0;     // solve-kernel variant: 0 mixed, 1 FP64 only, 2 FP32-refinement only
   int n_teams = 0;
   int n_active = 0;
   InstStatus *d_status_out = nullptr;
@@ -139,10 +141,10 @@ struct shell_batch {
 
 namespace {
 
-int blocks_per_sm_cached() {
-  static int n = -1;
-  if (n < 0) n = std::max(1, solve_blocks_per_sm());
-  return n;
+int blocks_per_sm_cached(int prec) {
+  static int n[3] = {-1, -1, -1};
+  if (n[prec] < 0) n[prec] = std::max(1, solve_blocks_per_sm(prec));
+  return n[prec];
 }
 int num_sms() {
   static int n = -1;
@@ -184,13 +186,18 @@ int rebuild_tables(shell_batch *b) {
       (h->h.precision == SHELL_FP64 ? t64 : t32).push_back(t);
     }
   }
-  // ---- schedule: teams of CTAs, each working through a list of instances
-  const int G = num_sms() * blocks_per_sm_cached();
+  // ---- solve-kernel variant by the precisions present, then the schedule: teams of CTAs, each working
+  // through a list of instances
+  bool any64 = false, any32 = false;
+  for (int k = 0; k < n; ++k) (b->slots[b->active[k]]->h.precision == SHELL_FP64 ? any64 : any32) = true;
+  b->prec = (any64 && any32) ? 0 : (any64 ? 1 : 2);
+  const int G = num_sms() * blocks_per_sm_cached(b->prec);
   std::vector<double> work(n);
   double total = 0.0;
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
     work[k] = (double)h->nv * std::max(1.0, h->est_iters);
+    h->sched_est = h->est_iters;
     total += work[k];
   }
   std::vector<int> order(n);
@@ -263,7 +270,7 @@ int rebuild_tables(shell_batch *b) {
     b->sched.team_size = C.take<int32_t>(n_teams);
     b->sched.team_ptr = C.take<int32_t>(n_teams + 1);
     b->sched.team_list = C.take<int32_t>(tlist.size());
-    b->sched.bar = C.take<unsigned int>((size_t)32 * n_teams);
+    b->sched.bar = C.take<unsigned int>((size_t)kBarWords * n_teams);
     b->sched.abort_flag = C.take<int32_t>(1);
     b->d_status_out = C.take<InstStatus>(n);
     b->d_abort_out = C.take<int32_t>(1);
@@ -291,7 +298,7 @@ int rebuild_tables(shell_batch *b) {
   CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_ptr, tptr.data(), 4 * (n_teams + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_list, tlist.data(), 4 * tlist.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * 32 * n_teams, st));
+  CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * kBarWords * n_teams, st));
   CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
   b->n_tiles64 = (int)t64.size();
@@ -304,7 +311,7 @@ int launch_step(shell_batch *b) {
   cudaStream_t st = b->mem.st;
   CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
   CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
-  CK(launch_solve(b->d_insts, b->sched, b->grid, st));
+  CK(launch_solve(b->d_insts, b->sched, b->grid, b->prec, st));
   return SHELL_OK;
 }
 
@@ -370,7 +377,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
       CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
       CK(cudaEventRecord(b->pev[3 * s + 1], st));
-      CK(launch_solve(b->d_insts, b->sched, b->grid, st));
+      CK(launch_solve(b->d_insts, b->sched, b->grid, b->prec, st));
       CK(cudaEventRecord(b->pev[3 * s + 2], st));
     } else if (b->gexec) {
       CK(cudaGraphLaunch(b->gexec, st));
@@ -402,7 +409,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   int first_err = SHELL_OK;
   if (aborted) {
     first_err = SHELL_ERR_TIMEOUT;
-    CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * 32 * b->n_teams, st));
+    CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * kBarWords * b->n_teams, st));
     CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
     CK(cudaStreamSynchronize(st));
   }
@@ -416,8 +423,10 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
     const int done = a.steps_done - z.steps_done;
     if (a.err != SHELL_OK && first_err == SHELL_OK) first_err = a.err;
     if (done > 0) {
-      const double it = a.last_iters + 2.0 * a.last_rounds;
-      h->est_iters = 0.5 * h->est_iters + 0.5 * std::max(1.0, it);
+      const double it = double(a.total_iters - z.total_iters + 2 * (a.total_rounds - z.total_rounds)) / done;
+      h->est_iters = std::max(1.0, it);
+      // results do not depend on the schedule, so re-plan freely when the work estimate moved
+      if (std::fabs(h->est_iters - h->sched_est) > 0.25 * h->sched_est) b->dirty = true;
     }
     if (stats) {
       shell_step_stats &o = stats[b->active[k]];
@@ -596,7 +605,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   I.precision = opt.precision;
   I.kt = T.kt;
   I.n_slices = T.n_slices;
-  I.rows_per_thread = nv > (1 << 20) ? 4 : (nv > (1 << 16) ? 2 : 1);
+  I.rows_per_thread = 1;
   const int chunk = kBlock * I.rows_per_thread;
   I.n_chunks = (nv + chunk - 1) / chunk;
   I.pcg_max_it = opt.pcg_max_it;
@@ -660,6 +669,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.val32 = C.take<float>(nnz_pad);
     I.dinv64 = C.take<double>(nv);
     I.dinv32 = C.take<float>(nv);
+    I.rs32 = C.take<float>(nv);
     I.diag_pos = C.take<int32_t>(nv);
     I.b = C.take<double>(3 * (size_t)nv);
     I.sol = C.take<double>(3 * (size_t)nv);
@@ -812,7 +822,8 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
 int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
   if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
-  int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(), h->h.n_chunks));
+  const int prec = h->h.precision == SHELL_FP64 ? 1 : 2;
+  int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(prec), h->h.n_chunks));
   if (team > static_max_ctas()) return SHELL_ERR_STATIC_LIMIT;
   const InstStatus before = h->last_status;
   InstStatus after{};

@@ -20,6 +20,9 @@ constexpr int kSlice = 32;          // SELL slice height (one warp)
 constexpr int kBlock = 256;         // threads of every CTA of the persistent solve kernel
 constexpr int kForceBlock = 128;    // threads of a force tile
 constexpr int kMaxTeamWaitMs = 4000;  // bounded spin of the team barrier
+constexpr int kBarWords = 64;       // barrier words per team: arrival count at [0], generation at [32]
+                                    // (separate 128-byte lines, so spinning readers do not contend with
+                                    // the arrival atomics)
 
 // stencil modes
 enum : uint8_t { MODE_PLATE = 0, MODE_SHELL = 1, MODE_FIXED = 2, MODE_NONE = 3 };
@@ -90,6 +93,7 @@ struct Inst {
   int32_t *sl_col;               // [nnz_pad]
   double *val64;  float *val32;  // [nnz_pad]
   double *dinv64; float *dinv32; // [nv] inverse diagonal (Jacobi)
+  float *rs32;                   // [nv] row sums of A (FP64 sum, rounded): FP32 SpMV in difference form
   int32_t *diag_pos;             // [nv]
   int32_t *asm_ptr, *asm_src;    // assembly sources of each SELL position
   double *local;                 // [n_local] per-stencil local matrix entries
@@ -122,7 +126,7 @@ struct Tile {
 struct Sched {
   int32_t *cta_team, *cta_rank;
   int32_t *team_size, *team_ptr, *team_list;
-  unsigned int *bar;     // [n_teams][32] barrier words (count at [0], generation at [16])
+  unsigned int *bar;     // [n_teams][kBarWords] barrier words
   int32_t *abort_flag;   // set when a bounded wait gives up
   int32_t n_ctas;
 };
@@ -135,7 +139,7 @@ cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles,
                           cudaStream_t st);
 cudaError_t launch_gather_forces(const Inst *d_inst, const Inst &h_inst, double *d_out, cudaStream_t st);
 cudaError_t launch_energy_reduce(const Inst *d_inst, const Inst &h_inst, double *d_out4, cudaStream_t st);
-cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cudaStream_t st);
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int nv, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int nv, cudaStream_t st);
 cudaError_t launch_mass(const Inst *d_inst, const Inst &h_inst, double rho, const double g[3], int n_loads,
@@ -144,7 +148,7 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
                                  int32_t *d_out_abort, cudaStream_t st);
 cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
                            cudaStream_t st);
-int solve_blocks_per_sm();
+int solve_blocks_per_sm(int prec);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
 int static_max_ctas();
 cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
                                int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st);

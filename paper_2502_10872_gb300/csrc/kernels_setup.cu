@@ -379,6 +379,7 @@ __global__ void k_assemble(const Inst *__restrict__ pI) {
   const double dt2 = I.dt * I.dt;
   const int dp = I.diag_pos[i];
   const bool pin_i = I.pinned[i] != 0;
+  double rowsum = 0.0;
   for (int k = 0; k < width; ++k) {
     const int p = base + 32 * k + lane;
     const int c = I.sl_col[p];
@@ -389,7 +390,9 @@ __global__ void k_assemble(const Inst *__restrict__ pI) {
     if (pin_i || I.pinned[c]) v = (p == dp) ? 1.0 : 0.0;
     I.val64[p] = v;
     I.val32[p] = (float)v;
+    rowsum += v;
   }
+  I.rs32[i] = (float)rowsum;
   const double dinv = 1.0 / I.val64[dp];
   I.dinv64[i] = dinv;
   I.dinv32[i] = (float)dinv;

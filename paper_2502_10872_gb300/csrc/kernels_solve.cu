@@ -63,7 +63,7 @@ __device__ bool team_sync(const Team &tm) {
   if (threadIdx.x == 0) {
     int ok = 1;
     unsigned int *count = tm.bar;
-    unsigned int *gen = tm.bar + 16;
+    unsigned int *gen = tm.bar + kBarWords / 2;
     const unsigned int g = ld_acquire(gen);
     __threadfence();
     const unsigned int arrived = atomicAdd(count, 1u);
@@ -191,20 +191,72 @@ __device__ inline float4 ldg4(const float4 *p) { return *p; }
 
 // y = A g for one row (SELL-32)
 // g is written by other CTAs during the launch: it must not be read through the non-coherent path, so it
-// carries no __restrict__ / const-restrict qualification.
-template <typename R, typename G>
-__device__ inline void spmv_row(const Inst &I, const R *__restrict__ val, const G *g, int row, R &ax, R &ay,
-                                R &az) {
+// carries no __restrict__ / const-restrict qualification. Both forms issue the column, value and gather
+// loads of several nonzeros before consuming them (memory-level parallelism per thread).
+//
+// FP64 (refinement residual, FP64 CG): y_i = sum_j a_ij g_j.
+__device__ inline void spmv_row(const Inst &I, const double *__restrict__ val, const D4 *g, int row, double &ax,
+                                double &ay, double &az) {
+  constexpr int U = 4;
   const int s = row >> 5, lane = row & 31;
-  const int b0 = I.sl_ptr[s], b1 = I.sl_ptr[s + 1];
-  ax = ay = az = R(0);
-  for (int p = b0 + lane; p < b1; p += 32) {
-    const int c = I.sl_col[p];
-    const R a = val[p];
-    const G v = ldg4(g + c);
-    ax += a * R(v.x);
-    ay += a * R(v.y);
-    az += a * R(v.z);
+  const int b1 = I.sl_ptr[s + 1];
+  ax = ay = az = 0.0;
+  for (int p = I.sl_ptr[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    double a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? I.sl_col[q] : row;
+      a[j] = ok ? val[q] : 0.0;
+    }
+    D4 v[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) v[j] = ldg4(g + c[j]);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      ax += a[j] * v[j].x;
+      ay += a[j] * v[j].y;
+      az += a[j] * v[j].z;
+    }
+  }
+}
+
+// FP32 (inner CG): difference form y_i = rs_i g_i + sum_{j != i} a_ij (g_j - g_i), rs_i = sum_j a_ij taken
+// in FP64. When dt^2 K dominates M, A's smallest eigenvalues come from the mass while its entries come from
+// the stiffness; rounding the entries to FP32 in the plain form would perturb those modes by more than
+// their size. In this form the rounding of a_ij only scales differences, and the constant mode sees the
+// accurately rounded row sum.
+__device__ inline void spmv_row(const Inst &I, const float *__restrict__ val, const float4 *g, int row, float &ax,
+                                float &ay, float &az) {
+  constexpr int U = 8;
+  const int s = row >> 5, lane = row & 31;
+  const int b1 = I.sl_ptr[s + 1];
+  const float4 ui = g[row];
+  const float rs = I.rs32[row];
+  ax = rs * ui.x;
+  ay = rs * ui.y;
+  az = rs * ui.z;
+  for (int p = I.sl_ptr[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    float a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? I.sl_col[q] : row;
+      a[j] = ok ? val[q] : 0.0f;
+    }
+    float4 v[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) v[j] = g[c[j]];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      ax += a[j] * (v[j].x - ui.x);
+      ay += a[j] * (v[j].y - ui.y);
+      az += a[j] * (v[j].z - ui.z);
+    }
   }
 }
 
@@ -270,7 +322,7 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
       const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
       if (row >= nv) continue;
       double ax, ay, az;
-      spmv_row<double, D4>(I, I.val64, g64, row, ax, ay, az);
+      spmv_row(I, I.val64, g64, row, ax, ay, az);
       const double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
       I.r64[row] = r0;
       I.r64[nv + row] = r1;
@@ -306,7 +358,7 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
       const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
       if (row >= nv) continue;
       R ax, ay, az;
-      spmv_row<R>(I, val, g, row, ax, ay, az);
+      spmv_row(I, val, g, row, ax, ay, az);
       w[row] = ax;
       w[nv + row] = ay;
       w[2 * nv + row] = az;
@@ -521,19 +573,26 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
   return true;
 }
 
-__global__ void __launch_bounds__(kBlock) k_solve(const Inst *__restrict__ insts, Sched sch) {
+// PREC: 0 = instances of either precision, 1 = FP64 instances only, 2 = FP32-refinement instances only (the
+// single-precision variants need fewer registers, so more CTAs fit on an SM).
+template <int PREC>
+__global__ void __launch_bounds__(kBlock, PREC == 2 ? 3 : 2) k_solve(const Inst *__restrict__ insts, Sched sch) {
   Team tm;
   tm.team = sch.cta_team[blockIdx.x];
   if (tm.team < 0) return;
   tm.rank = sch.cta_rank[blockIdx.x];
   tm.size = sch.team_size[tm.team];
-  tm.bar = sch.bar + 32 * tm.team;
+  tm.bar = sch.bar + kBarWords * tm.team;
   tm.abort_flag = sch.abort_flag;
   tm.bank = 0;
   for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
     const Inst &I = insts[sch.team_list[q]];
     if (I.status->err != SHELL_OK) continue;
-    const bool ok = (I.precision == SHELL_FP64) ? solve_fp64(I, tm) : solve_fp32r(I, tm);
+    bool ok;
+    if (PREC == 1 || (PREC == 0 && I.precision == SHELL_FP64))
+      ok = solve_fp64(I, tm);
+    else
+      ok = solve_fp32r(I, tm);
     if (!ok) return;
     // make this instance's final writes (status) ordered before the team moves on
     if (!team_sync(tm)) return;
@@ -542,13 +601,18 @@ __global__ void __launch_bounds__(kBlock) k_solve(const Inst *__restrict__ insts
 
 }  // namespace
 
-int solve_blocks_per_sm() {
+int solve_blocks_per_sm(int prec) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve, kBlock, 0);
+  if (prec == 1)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<1>, kBlock, 0);
+  else if (prec == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<2>, kBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<0>, kBlock, 0);
   return n;
 }
 
-cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cudaStream_t st) {
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
@@ -559,7 +623,9 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cuda
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_solve, d_insts, sched);
+  if (prec == 1) return cudaLaunchKernelEx(&cfg, k_solve<1>, d_insts, sched);
+  if (prec == 2) return cudaLaunchKernelEx(&cfg, k_solve<2>, d_insts, sched);
+  return cudaLaunchKernelEx(&cfg, k_solve<0>, d_insts, sched);
 }
 
 // ---------------------------------------------------------------- step without device allocation
@@ -567,9 +633,12 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, cuda
 // for callers that cannot allocate device memory: it lives in this file-scope array, which every GPU that
 // loads the library holds until the process exits. Layout (32-bit words): [0, kStaticMaxCtas) team of each
 // CTA, [kStaticMaxCtas, 2 kStaticMaxCtas) rank, then team_size[1], team_ptr[2], team_list[1], the barrier
-// words (32), the abort flag, its read-back copy, and one InstStatus.
+// words (kBarWords), the abort flag, its read-back copy, and one InstStatus.
 constexpr int kStaticMaxCtas = 2048;
-constexpr int kStaticWords = 2 * kStaticMaxCtas + 4 + 32 + 2 + 64;
+constexpr int kStaticBar = 2 * kStaticMaxCtas + 32;                 // 128-byte aligned word offset
+constexpr int kStaticAbort = kStaticBar + kBarWords;                // abort flag, then its read-back copy
+constexpr int kStaticStatus = kStaticAbort + 8;                     // one InstStatus (8-byte aligned)
+constexpr int kStaticWords = kStaticStatus + (int)(sizeof(InstStatus) / 4) + 4;
 static __device__ __align__(256) unsigned int g_static_scratch[kStaticWords];
 
 namespace {
@@ -608,10 +677,10 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   sc.team_size = w + 2 * kStaticMaxCtas;
   sc.team_ptr = w + 2 * kStaticMaxCtas + 1;
   sc.team_list = w + 2 * kStaticMaxCtas + 3;
-  sc.bar = base + 2 * kStaticMaxCtas + 4;
-  sc.abort_flag = w + 2 * kStaticMaxCtas + 4 + 32;
+  sc.bar = base + kStaticBar;
+  sc.abort_flag = w + kStaticAbort;
   int32_t *abort_out = sc.abort_flag + 1;
-  InstStatus *status_out = reinterpret_cast<InstStatus *>(base + 2 * kStaticMaxCtas + 4 + 32 + 2 + 2);
+  InstStatus *status_out = reinterpret_cast<InstStatus *>(base + kStaticStatus);
   sc.n_ctas = team_ctas;
   static thread_local int32_t host_tab[2 * kStaticMaxCtas + 4];
   for (int c = 0; c < team_ctas; ++c) {
@@ -629,10 +698,10 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   if ((e = cudaMemcpyAsync(sc.team_size, host_tab + 2 * kStaticMaxCtas, 16, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
   // the barrier words and the abort flag must start at zero; the array keeps the previous call's contents
-  if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (32 + 2), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (kBarWords + 2), st)) != cudaSuccess) return e;
   for (int k = 0; k < n_steps; ++k) {
     if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st)) != cudaSuccess) return e;
-    if ((e = launch_solve(d_inst, sc, team_ctas, st)) != cudaSuccess) return e;
+    if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, st)) != cudaSuccess) return e;
   }
   if ((e = launch_gather_status(d_inst, 1, status_out, sc.abort_flag, abort_out, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(h_status, status_out, sizeof(InstStatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -641,7 +710,7 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
     return e;
   e = cudaStreamSynchronize(st);
   if (e == cudaSuccess && *h_aborted) {
-    cudaMemsetAsync(sc.bar, 0, 4 * (32 + 2), st);
+    cudaMemsetAsync(sc.bar, 0, 4 * (kBarWords + 2), st);
     e = cudaStreamSynchronize(st);
   }
   return e;

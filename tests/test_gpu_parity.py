@@ -188,7 +188,7 @@ def test_full_size_jittered_plate_step_satisfies_system():
     after 3 steps, one more step is checked against the oracle's own system at that state:
     |A v' - b| <= 1.5 refine_rtol |b| with A, b built by the oracle, and x' = x + dt v'."""
     sc = sg.jittered_plate(512)
-    h = gb.create_from_scenario(sc, precision="fp32_refine", refine_rtol=1e-10)
+    h = gb.create_from_scenario(sc, precision="fp32_refine", refine_rtol=1e-10, refine_max=40, pcg_max_it=60000)
     gb.shell_step(h, 3)
     x, v = gb.shell_get_state(h)
     st = gb.shell_step(h, 1)
