@@ -1,0 +1,161 @@
+"""Continuous-batching request loop over the C-ABI batch (argument marshalling and scheduling only).
+
+Requests (meshes with a step count) arrive over time. A request is admitted as soon as the batch's HBM
+budget holds its instance: its handle is created (host topology plus the GPU precompute and assembly) on a
+worker thread while the GPU steps the resident instances, then it joins the batch between two steps. Every
+step advances all resident instances in one force launch and one persistent solve launch. A request retires
+(and frees its device memory) after its last step. Each instance's result does not depend on the others
+in the batch (deterministic, team-size independent reductions), so a request gives the same state alone or
+in any mix.
+
+Reported: aggregate vertex-steps/s over the wall time, per-step device latency p50/p99 of the batch, the
+queueing delay (arrival to admission) and per-request completion times.
+"""
+from __future__ import annotations
+
+import dataclasses
+import threading
+import time
+from collections import deque
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import binding as gb
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    scenario: object            # anything create_from_scenario accepts
+    steps: int
+    handle: Optional[gb.Handle] = None
+    slot: int = -1
+    done_steps: int = 0
+    admitted_s: float = float("nan")
+    finished_s: float = float("nan")
+    status: int = 0
+    final_state: Optional[tuple] = None
+
+
+@dataclasses.dataclass
+class ServeReport:
+    wall_s: float
+    vertex_steps: int
+    steps: int
+    step_ms: np.ndarray
+    requests: List[Request]
+
+    @property
+    def vertex_steps_per_s(self) -> float:
+        return self.vertex_steps / self.wall_s if self.wall_s > 0 else 0.0
+
+    def summary(self) -> dict:
+        lat = self.step_ms
+        q = [r.admitted_s - r.arrival_s for r in self.requests if np.isfinite(r.admitted_s)]
+        return {
+            "requests": len(self.requests),
+            "completed": sum(1 for r in self.requests if np.isfinite(r.finished_s)),
+            "failed": sum(1 for r in self.requests if r.status != 0),
+            "batch_steps": self.steps,
+            "vertex_steps": self.vertex_steps,
+            "vertex_steps_per_s": self.vertex_steps_per_s,
+            "wall_s": self.wall_s,
+            "step_ms_p50": float(np.percentile(lat, 50)) if len(lat) else None,
+            "step_ms_p99": float(np.percentile(lat, 99)) if len(lat) else None,
+            "queue_s_p50": float(np.percentile(q, 50)) if q else None,
+            "queue_s_p99": float(np.percentile(q, 99)) if q else None,
+        }
+
+
+class Server:
+    """Admit requests into one batch by an HBM budget and step them together."""
+
+    def __init__(self, budget_bytes: int, precision: str = "fp32_refine", keep_states: bool = False,
+                 create_kw: Optional[dict] = None, clock: Callable[[], float] = time.perf_counter):
+        self.budget = int(budget_bytes)
+        self.precision = precision
+        self.keep_states = keep_states
+        self.create_kw = create_kw or {}
+        self.clock = clock
+        self.batch = gb.shell_batch_create(self.budget)
+        self.used = 0
+
+    def _create(self, req: Request):
+        req.handle = gb.create_from_scenario(req.scenario, precision=self.precision, **self.create_kw)
+
+    def run(self, requests: List[Request], max_wall_s: float = 1e9, steps_per_launch: int = 1) -> ServeReport:
+        pending = deque(sorted(requests, key=lambda r: r.arrival_s))
+        ready: deque = deque()          # created handles waiting for budget
+        active: dict = {}               # slot -> request
+        lat: list = []
+        vsteps = 0
+        nsteps = 0
+        t0 = self.clock()
+        worker: Optional[threading.Thread] = None
+        building: Optional[Request] = None
+
+        def now():
+            return self.clock() - t0
+
+        while pending or ready or active or building is not None:
+            if now() > max_wall_s:
+                break
+            # start building the next arrived request on the worker thread (overlaps the GPU step)
+            if worker is None and pending and pending[0].arrival_s <= now():
+                building = pending.popleft()
+                worker = threading.Thread(target=self._create, args=(building,))
+                worker.start()
+            if worker is not None and not worker.is_alive():
+                worker.join()
+                ready.append(building)
+                worker, building = None, None
+            # admit what fits the budget
+            while ready:
+                req = ready[0]
+                rc = gb.shell_batch_admit(self.batch, req.handle, check=False)
+                if isinstance(rc, int) and rc == gb.SHELL_ERR_BUDGET:
+                    break
+                if isinstance(rc, int) and rc < 0:
+                    raise gb.ShellError(rc, "shell_batch_admit")
+                req.slot = rc
+                req.admitted_s = now()
+                active[req.slot] = req
+                ready.popleft()
+            if not active:
+                if worker is not None:
+                    worker.join(timeout=0.001)
+                elif pending:
+                    time.sleep(min(0.001, max(0.0, pending[0].arrival_s - now())))
+                continue
+            # one batch step for every resident instance
+            n = steps_per_launch
+            rc, stats = gb.shell_batch_step(self.batch, n, check=False)
+            lat.extend(gb.shell_batch_step_times(self.batch, n).tolist())
+            nsteps += n
+            for slot, req in list(active.items()):
+                st = stats.get(slot)
+                if st is None:
+                    continue
+                req.done_steps += st["steps_done"]
+                vsteps += st["steps_done"] * req.scenario.n_verts
+                if st["status"] != 0:
+                    req.status = st["status"]
+                if req.done_steps >= req.steps or req.status != 0:
+                    req.finished_s = now()
+                    if self.keep_states:
+                        req.final_state = gb.shell_get_state(req.handle)
+                    gb.shell_batch_retire(self.batch, slot)
+                    gb.shell_destroy(req.handle)
+                    req.handle = None
+                    del active[slot]
+        wall = now()
+        if worker is not None:
+            worker.join()
+        return ServeReport(wall, vsteps, nsteps, np.asarray(lat, np.float64), list(requests))
+
+    def close(self):
+        if self.batch is not None:
+            gb.shell_batch_destroy(self.batch)
+            self.batch = None
