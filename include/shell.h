@@ -111,6 +111,13 @@ typedef struct shell_bc {
 typedef void *(*shell_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
 typedef void (*shell_free_fn)(void *ptr, size_t bytes, void *cuda_stream, void *user);
 
+/* Preconditioner of the PCG. AUTO: smoothed-aggregation multigrid when the step matrix is stiff
+ * (median dt^2 K_ii / m_i > 30 and V >= 256), else Jacobi. AMG: the multigrid hierarchy is built once at
+ * shell_create from the assembled matrix (it never changes) and applied as one V(1,1) cycle per
+ * iteration. */
+typedef enum shell_preconditioner { SHELL_PRECOND_AUTO = 0, SHELL_PRECOND_JACOBI = 1, SHELL_PRECOND_AMG = 2 }
+    shell_preconditioner;
+
 typedef struct shell_options {
   double dt;               /* time step > 0 */
   int32_t precision;       /* shell_precision */
@@ -122,10 +129,12 @@ typedef struct shell_options {
   shell_alloc_fn alloc;    /* optional device allocator */
   shell_free_fn free;
   void *alloc_user;
+  int32_t preconditioner;  /* shell_preconditioner */
 } shell_options;
 
 /* Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
- * FP64 PCG, 1e-4 for the inner FP32 PCG, 1e-10 for the refinement), pcg_max_it 20000, refine_max 20. */
+ * FP64 PCG, 1e-4 for the inner FP32 PCG, 1e-10 for the refinement), pcg_max_it 20000, refine_max 20,
+ * preconditioner AUTO. */
 void shell_default_options(shell_options *opt);
 
 /* Statistics of the last shell_step / shell_batch_step call for one instance. */
@@ -192,8 +201,8 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
 
 /* Sizes: out[0] vertices, out[1] triangles, out[2] bending stencils, out[3] bytes of device memory the handle
  * holds, out[4] structural nonzeros of the scalar matrix, out[5] stored (SELL-padded) nonzeros, out[6]
- * force contribution slots. */
-int shell_info(shell_handle *h, int64_t out[7]);
+ * force contribution slots, out[7] multigrid levels (0 = Jacobi preconditioner). */
+int shell_info(shell_handle *h, int64_t out[8]);
 
 int shell_destroy(shell_handle *h);
 const char *shell_strerror(int code);

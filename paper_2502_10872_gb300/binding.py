@@ -30,6 +30,7 @@ for _c, _n in ERRORS.items():
     globals()[_n] = _c
 MODELS = {"EP": 0, "ES": 1, "FP": 2, "FS": 3, "SP": 4, "SS": 5}
 PRECISIONS = {"fp64": 0, "fp32_refine": 1}
+PRECONDITIONERS = {"auto": 0, "jacobi": 1, "amg": 2}
 
 # symbols declared in include/shell.h
 EXPORTS = (
@@ -76,7 +77,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class shell_options(C.Structure):
     _fields_ = [("dt", C.c_double), ("precision", C.c_int32), ("pcg_rtol", C.c_double),
                 ("refine_rtol", C.c_double), ("pcg_max_it", C.c_int32), ("refine_max", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("preconditioner", C.c_int32)]
 
 
 class shell_step_stats(C.Structure):
@@ -189,7 +191,8 @@ def _current_stream():
 
 
 def make_options(dt=1e-2, precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
-                 stream: Optional[int] = None, use_torch_allocator: bool = True) -> shell_options:
+                 stream: Optional[int] = None, use_torch_allocator: bool = True,
+                 preconditioner="auto") -> shell_options:
     lib = load_library()
     o = shell_options()
     lib.shell_default_options(C.byref(o))
@@ -199,6 +202,7 @@ def make_options(dt=1e-2, precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_m
     o.refine_rtol = float(refine_rtol)
     o.pcg_max_it = int(pcg_max_it)
     o.refine_max = int(refine_max)
+    o.preconditioner = PRECONDITIONERS[preconditioner] if isinstance(preconditioner, str) else int(preconditioner)
     o.cuda_stream = _current_stream() if stream is None else int(stream)
     hooks = _torch_allocator() if use_torch_allocator else None
     if hooks:
@@ -241,7 +245,7 @@ class Handle:
 def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None, init_vel=None, pinned=None,
                  clamped_edges=None, gravity=(0.0, 0.0, 0.0), load_vtx=None, load_f=None, dt=1e-2,
                  precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
-                 stream=None, use_torch_allocator=True) -> Handle:
+                 stream=None, use_torch_allocator=True, preconditioner="auto") -> Handle:
     """shell_create: rest-state precompute and constant-matrix assembly on the GPU (see include/shell.h)."""
     lib = load_library()
     tris = _arr(tris, np.int32, (-1, 3))
@@ -263,7 +267,8 @@ def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None,
     bc.n_loads = lv.shape[0]
     bc.load_vtx = _ptr(lv) if lv.shape[0] else None
     bc.load_f = _ptr(lf) if lv.shape[0] else None
-    opts = make_options(dt, precision, pcg_rtol, refine_rtol, pcg_max_it, refine_max, stream, use_torch_allocator)
+    opts = make_options(dt, precision, pcg_rtol, refine_rtol, pcg_max_it, refine_max, stream, use_torch_allocator,
+                        preconditioner)
     out = C.c_void_p()
     m = MODELS[model] if isinstance(model, str) else int(model)
     _check(lib.shell_create(C.byref(mesh), C.byref(mat), m, C.byref(bc), C.byref(opts), C.byref(out)), "shell_create")
@@ -346,10 +351,10 @@ def shell_set_state_device(h: Handle, x_dev=None, v_dev=None):
 
 
 def shell_info(h: Handle) -> dict:
-    out = np.zeros(7, np.int64)
+    out = np.zeros(8, np.int64)
     _check(load_library().shell_info(h.ptr, out.ctypes.data), "shell_info")
     return {"n_verts": int(out[0]), "n_tris": int(out[1]), "n_stencils": int(out[2]), "device_bytes": int(out[3]),
-            "nnz": int(out[4]), "nnz_stored": int(out[5]), "n_slots": int(out[6])}
+            "nnz": int(out[4]), "nnz_stored": int(out[5]), "n_slots": int(out[6]), "amg_levels": int(out[7])}
 
 
 def shell_destroy(h: Handle):

@@ -1,0 +1,309 @@
+// amg_setup.cpp -- smoothed-aggregation algebraic multigrid (Vanek, Mandel, Brezina 1996) for the
+// constant step matrix A = M + dt^2 K. The matrix never changes, so the hierarchy is built once per mesh;
+// the V-cycle runs inside the persistent solve kernel as the PCG preconditioner.
+//
+//   strength    |a_ij| >= theta sqrt(a_ii a_jj)
+//   aggregates  greedy: a node whose strong neighbours are all free roots an aggregate with them; leftover
+//               nodes join a neighbouring aggregate; the rest form their own
+//   P           (I - omega D^-1 A) P0, P0 the aggregate indicator (near-null space: constants), omega = 4/(3 rho)
+//   A_c         P^T A P (Galerkin), repeated until the level is small; the coarsest is inverted densely
+#include "amg_setup.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace shl {
+
+namespace {
+
+HostCsr transpose(const HostCsr &M) {
+  HostCsr T;
+  T.n = M.m;
+  T.m = M.n;
+  T.ptr.assign(T.n + 1, 0);
+  for (int32_t c : M.col) T.ptr[c + 1]++;
+  for (int i = 0; i < T.n; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(M.col.size());
+  T.val.resize(M.val.size());
+  std::vector<int32_t> fill(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < M.n; ++i)
+    for (int q = M.ptr[i]; q < M.ptr[i + 1]; ++q) {
+      int k = fill[M.col[q]]++;
+      T.col[k] = i;
+      T.val[k] = M.val[q];
+    }
+  return T;
+}
+
+// C = A * B (sparse, rows accumulated with a dense marker)
+HostCsr multiply(const HostCsr &A, const HostCsr &B) {
+  HostCsr C;
+  C.n = A.n;
+  C.m = B.m;
+  C.ptr.assign(C.n + 1, 0);
+  std::vector<int32_t> mark(B.m, -1);
+  std::vector<double> acc(B.m, 0.0);
+  std::vector<int32_t> cols;
+  for (int i = 0; i < A.n; ++i) {
+    cols.clear();
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) {
+      const int k = A.col[q];
+      const double a = A.val[q];
+      for (int r = B.ptr[k]; r < B.ptr[k + 1]; ++r) {
+        const int j = B.col[r];
+        if (mark[j] != i) {
+          mark[j] = i;
+          acc[j] = 0.0;
+          cols.push_back(j);
+        }
+        acc[j] += a * B.val[r];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int j : cols) {
+      C.col.push_back(j);
+      C.val.push_back(acc[j]);
+    }
+    C.ptr[i + 1] = (int32_t)C.col.size();
+  }
+  return C;
+}
+
+double diag_of(const HostCsr &A, int i) {
+  for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
+    if (A.col[q] == i) return A.val[q];
+  return 0.0;
+}
+
+// spectral radius of D^-1 A by power iteration (an upper estimate is fine for the weights)
+double rho_dinv_a(const HostCsr &A, const std::vector<double> &dinv) {
+  const int n = A.n;
+  std::vector<double> x(n), y(n);
+  for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * std::sin(1.7 * i + 0.3);
+  double lam = 1.0;
+  for (int it = 0; it < 20; ++it) {
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
+      y[i] = dinv[i] * s;
+      nrm += y[i] * y[i];
+    }
+    nrm = std::sqrt(nrm);
+    double xn = 0.0;
+    for (int i = 0; i < n; ++i) xn += x[i] * x[i];
+    lam = nrm / std::sqrt(xn);
+    if (!(nrm > 0)) break;
+    for (int i = 0; i < n; ++i) x[i] = y[i] / nrm;
+  }
+  return lam * 1.05;   // safety margin for the unconverged power iteration
+}
+
+// returns the number of aggregates; agg[i] = -1 for rows left out (isolated)
+int aggregate(const HostCsr &A, double theta, std::vector<int32_t> &agg) {
+  const int n = A.n;
+  std::vector<double> d(n);
+  for (int i = 0; i < n; ++i) d[i] = std::fabs(diag_of(A, i));
+  auto strong = [&](int i, int q) {
+    const int j = A.col[q];
+    return j != i && std::fabs(A.val[q]) >= theta * std::sqrt(d[i] * d[j]);
+  };
+  agg.assign(n, -2);   // -2 = free
+  int na = 0;
+  std::vector<char> isolated(n, 0);
+  for (int i = 0; i < n; ++i) {
+    bool any = false;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) any |= strong(i, q);
+    if (!any) {
+      isolated[i] = 1;
+      agg[i] = -1;
+    }
+  }
+  // pass 1: roots whose strong neighbourhood is entirely free
+  for (int i = 0; i < n; ++i) {
+    if (agg[i] != -2) continue;
+    bool free_nb = true;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1] && free_nb; ++q)
+      if (strong(i, q) && agg[A.col[q]] != -2) free_nb = false;
+    if (!free_nb) continue;
+    agg[i] = na;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
+      if (strong(i, q)) agg[A.col[q]] = na;
+    ++na;
+  }
+  // pass 2: join the strongest aggregated neighbour
+  std::vector<int32_t> agg1 = agg;
+  for (int i = 0; i < n; ++i) {
+    if (agg[i] != -2) continue;
+    double best = -1.0;
+    int ba = -2;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
+      if (strong(i, q) && agg[A.col[q]] >= 0 && std::fabs(A.val[q]) > best) {
+        best = std::fabs(A.val[q]);
+        ba = agg[A.col[q]];
+      }
+    agg1[i] = ba;
+  }
+  agg = agg1;
+  // pass 3: what is left forms aggregates with its free strong neighbours
+  for (int i = 0; i < n; ++i) {
+    if (agg[i] != -2) continue;
+    agg[i] = na;
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q)
+      if (strong(i, q) && agg[A.col[q]] == -2) agg[A.col[q]] = na;
+    ++na;
+  }
+  return na;
+}
+
+bool dense_inverse(const HostCsr &A, std::vector<double> &inv) {
+  const int n = A.n;
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) L[(size_t)i * n + A.col[q]] = A.val[q];
+  // Cholesky (lower), in place
+  for (int j = 0; j < n; ++j) {
+    double s = L[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(s > 0)) return false;
+    const double ljj = std::sqrt(s);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = L[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<double> e(n), y(n);
+  for (int c = 0; c < n; ++c) {
+    std::fill(e.begin(), e.end(), 0.0);
+    e[c] = 1.0;
+    for (int i = 0; i < n; ++i) {
+      double t = e[i];
+      for (int k = 0; k < i; ++k) t -= L[(size_t)i * n + k] * y[k];
+      y[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < n; ++k) t -= L[(size_t)k * n + i] * e[k];
+      e[i] = t / L[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = e[i];
+  }
+  return true;
+}
+
+void finish_level(HostAmgLevel &L) {
+  const int n = L.A.n;
+  L.dinv.resize(n);
+  L.rowsum.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int q = L.A.ptr[i]; q < L.A.ptr[i + 1]; ++q) s += L.A.val[q];
+    L.rowsum[i] = s;
+    L.dinv[i] = 1.0 / diag_of(L.A, i);
+  }
+  L.omega = 4.0 / (3.0 * rho_dinv_a(L.A, L.dinv));
+}
+
+}  // namespace
+
+void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, double theta) {
+  HostAmg &H = *out;
+  H = HostAmg();
+  H.levels.emplace_back();
+  H.levels[0].A = A0;
+  finish_level(H.levels[0]);
+  while ((int)H.levels.size() < max_levels) {
+    HostAmgLevel &F = H.levels.back();
+    const int n = F.A.n;
+    if (n <= coarse_max) break;
+    std::vector<int32_t> agg;
+    const int na = aggregate(F.A, theta, agg);
+    if (na == 0 || na > (int)(0.8 * n)) break;   // coarsening stalled
+    // P = (I - omega D^-1 A) P0
+    HostCsr P;
+    P.n = n;
+    P.m = na;
+    P.ptr.assign(n + 1, 0);
+    std::vector<int32_t> mark(na, -1);
+    std::vector<double> acc(na, 0.0);
+    std::vector<int32_t> cols;
+    for (int i = 0; i < n; ++i) {
+      cols.clear();
+      auto add = [&](int c, double v) {
+        if (mark[c] != i) {
+          mark[c] = i;
+          acc[c] = 0.0;
+          cols.push_back(c);
+        }
+        acc[c] += v;
+      };
+      if (agg[i] >= 0) add(agg[i], 1.0);
+      if (agg[i] != -1) {   // rows left out (isolated) get no prolongation
+        for (int q = F.A.ptr[i]; q < F.A.ptr[i + 1]; ++q) {
+          const int j = F.A.col[q];
+          if (agg[j] >= 0) add(agg[j], -F.omega * F.dinv[i] * F.A.val[q]);
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      for (int c : cols)
+        if (acc[c] != 0.0) {
+          P.col.push_back(c);
+          P.val.push_back(acc[c]);
+        }
+      P.ptr[i + 1] = (int32_t)P.col.size();
+    }
+    F.P = P;
+    F.R = transpose(P);
+    HostCsr Ac = multiply(F.R, multiply(F.A, P));
+    H.levels.emplace_back();
+    H.levels.back().A = Ac;
+    finish_level(H.levels.back());
+  }
+  HostAmgLevel &C = H.levels.back();
+  if (C.A.n <= coarse_max && dense_inverse(C.A, H.coarse_inv)) {
+    H.coarse_sweeps = 0;
+  } else {
+    H.coarse_inv.clear();
+    H.coarse_sweeps = 8;
+  }
+}
+
+HostSell to_sell(const HostCsr &M) {
+  HostSell S;
+  S.n = M.n;
+  S.n_slices = (M.n + 31) / 32;
+  S.sl_ptr.assign(S.n_slices + 1, 0);
+  for (int s = 0; s < S.n_slices; ++s) {
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int r = s * 32 + l;
+      if (r < M.n) w = std::max(w, M.ptr[r + 1] - M.ptr[r]);
+    }
+    S.sl_ptr[s + 1] = S.sl_ptr[s] + 32 * w;
+  }
+  const int nnz = S.sl_ptr[S.n_slices];
+  S.sl_col.assign(nnz, 0);
+  S.val.assign(nnz, 0.0);
+  for (int s = 0; s < S.n_slices; ++s) {
+    const int w = (S.sl_ptr[s + 1] - S.sl_ptr[s]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int r = s * 32 + l;
+      for (int k = 0; k < w; ++k) {
+        const int pos = S.sl_ptr[s] + 32 * k + l;
+        if (r < M.n && k < M.ptr[r + 1] - M.ptr[r]) {
+          S.sl_col[pos] = M.col[M.ptr[r] + k];
+          S.val[pos] = M.val[M.ptr[r] + k];
+        } else {
+          S.sl_col[pos] = 0;
+          S.val[pos] = 0.0;
+        }
+      }
+    }
+  }
+  return S;
+}
+
+}  // namespace shl

@@ -1,0 +1,42 @@
+// amg_setup.h -- smoothed-aggregation multigrid hierarchy of the constant step matrix (host, once per mesh).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace shl {
+
+struct HostCsr {
+  int n = 0, m = 0;                 // rows, columns
+  std::vector<int32_t> ptr, col;
+  std::vector<double> val;
+};
+
+// SELL-32 image of a CSR matrix (padding: own row / column 0 with value 0)
+struct HostSell {
+  int n = 0, n_slices = 0;
+  std::vector<int32_t> sl_ptr, sl_col;
+  std::vector<double> val;
+};
+
+struct HostAmgLevel {
+  HostCsr A;                        // level operator (level 0: the step matrix)
+  HostCsr P;                        // prolongation: rows of this level -> columns of the next
+  HostCsr R;                        // restriction P^T
+  std::vector<double> dinv;         // 1 / diag(A)
+  std::vector<double> rowsum;       // sum_j A_ij (FP64)
+  double omega = 0.0;               // damped-Jacobi weight 4 / (3 rho(D^-1 A))
+};
+
+struct HostAmg {
+  std::vector<HostAmgLevel> levels; // levels[L-1] is the coarsest
+  std::vector<double> coarse_inv;   // dense inverse of the coarsest operator (row-major), empty if none
+  int coarse_sweeps = 0;            // Jacobi sweeps on the coarsest level when it is too large to invert
+};
+
+// Builds the hierarchy of the SPD matrix A (CSR, diagonal present). Rows whose only entry is the diagonal
+// (pinned vertices) are left out of the coarse spaces: the smoother solves them exactly.
+void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_max = 192, double theta = 0.08);
+
+HostSell to_sell(const HostCsr &M);
+
+}  // namespace shl

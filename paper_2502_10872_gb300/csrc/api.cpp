@@ -7,6 +7,7 @@
 #include <numeric>
 #include <vector>
 
+#include "amg_setup.h"
 #include "host_mesh.h"
 #include "internal.h"
 
@@ -103,6 +104,8 @@ struct shell_handle {
   shell_batch *solo = nullptr;   // private batch used by shell_step
   std::vector<Tile> tiles;       // force tiles of this instance (inst index filled by the batch)
   Tile *d_tiles = nullptr;       // the same tiles on the device (inst index 0 = d_inst)
+  void *amg_block = nullptr;     // multigrid hierarchy (device), if any
+  size_t amg_bytes = 0;
   double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
   double sched_est = 64.0;       // estimate the current schedule was planned with
   int64_t nnz = 0, nnz_pad = 0;
@@ -515,6 +518,155 @@ std::vector<double> to_soa(const double *aos, int nv) {
   return s;
 }
 
+// Multigrid preconditioner: download the assembled FP64 matrix, build the smoothed-aggregation hierarchy
+// on the host (the matrix is constant, so this happens once) and upload it as SELL-32 levels.
+int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
+  Inst &I = h->h;
+  cudaStream_t st = h->mem.st;
+  if (mode == SHELL_PRECOND_JACOBI) return SHELL_OK;
+  const int nv = I.nv;
+  const size_t nnz_pad = (size_t)T.sl_ptr[T.n_slices];
+  std::vector<double> val(nnz_pad), mass(nv);
+  CK(cudaMemcpyAsync(val.data(), I.val64, 8 * nnz_pad, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(mass.data(), I.mass, 8 * (size_t)nv, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  HostCsr A;
+  A.n = A.m = nv;
+  A.ptr = T.row_ptr;
+  A.col.resize(T.row_ptr[nv]);
+  A.val.resize(T.row_ptr[nv]);
+  std::vector<double> q;
+  for (int r = 0; r < nv; ++r) {
+    const int s = r / 32, l = r % 32;
+    for (int k = 0; k < T.row_ptr[r + 1] - T.row_ptr[r]; ++k) {
+      const int pos = T.sl_ptr[s] + 32 * k + l;
+      A.col[T.row_ptr[r] + k] = T.sl_col[pos];
+      A.val[T.row_ptr[r] + k] = val[pos];
+    }
+    const double d = val[T.diag_pos[r]];
+    if (mass[r] > 0 && T.row_ptr[r + 1] - T.row_ptr[r] > 1) q.push_back((d - mass[r]) / mass[r]);
+  }
+  if (mode == SHELL_PRECOND_AUTO) {
+    if (nv < 256 || q.empty()) return SHELL_OK;
+    std::nth_element(q.begin(), q.begin() + q.size() / 2, q.end());
+    if (q[q.size() / 2] <= 30.0) return SHELL_OK;
+  }
+  HostAmg H;
+  build_amg(A, &H);
+  const int L = (int)H.levels.size();
+  if (L < 2) return SHELL_OK;
+  std::vector<HostSell> As(L), Ps(L), Rs(L);
+  for (int l = 0; l < L; ++l) {
+    if (l > 0) As[l] = to_sell(H.levels[l].A);
+    if (l < L - 1) {
+      Ps[l] = to_sell(H.levels[l].P);
+      Rs[l] = to_sell(H.levels[l].R);
+    }
+  }
+  const int nc = H.levels[L - 1].A.n;
+  std::vector<AmgDev> lev(L);
+  double *cinv64 = nullptr;
+  float *cinv32 = nullptr;
+  AmgDev *d_lev = nullptr;
+  auto layout = [&](Carver &C) {
+    for (int l = 0; l < L; ++l) {
+      AmgDev &D = lev[l];
+      const int n = H.levels[l].A.n;
+      D.n = n;
+      D.n_next = (l < L - 1) ? H.levels[l + 1].A.n : 0;
+      D.omega = H.levels[l].omega;
+      if (l > 0) {
+        D.a_ptr = C.take<int32_t>(As[l].sl_ptr.size());
+        D.a_col = C.take<int32_t>(As[l].sl_col.size());
+        D.a_val32 = C.take<float>(As[l].val.size());
+        D.a_val64 = C.take<double>(As[l].val.size());
+        D.rs32 = C.take<float>(n);
+        D.dinv32 = C.take<float>(n);
+        D.dinv64 = C.take<double>(n);
+      } else {
+        D.a_ptr = I.sl_ptr;
+        D.a_col = I.sl_col;
+        D.a_val32 = I.val32;
+        D.a_val64 = I.val64;
+        D.rs32 = I.rs32;
+        D.dinv32 = I.dinv32;
+        D.dinv64 = I.dinv64;
+      }
+      if (l < L - 1) {
+        D.p_ptr = C.take<int32_t>(Ps[l].sl_ptr.size());
+        D.p_col = C.take<int32_t>(Ps[l].sl_col.size());
+        D.p_val32 = C.take<float>(Ps[l].val.size());
+        D.p_val64 = C.take<double>(Ps[l].val.size());
+        D.r_ptr = C.take<int32_t>(Rs[l].sl_ptr.size());
+        D.r_col = C.take<int32_t>(Rs[l].sl_col.size());
+        D.r_val32 = C.take<float>(Rs[l].val.size());
+        D.r_val64 = C.take<double>(Rs[l].val.size());
+      }
+      D.b = C.take<double>(4 * (size_t)n);
+      D.x = C.take<double>(4 * (size_t)n);
+      D.r = C.take<double>(4 * (size_t)n);
+      D.y = C.take<double>(4 * (size_t)n);
+    }
+    cinv64 = C.take<double>(H.coarse_inv.size());
+    cinv32 = C.take<float>(H.coarse_inv.size());
+    d_lev = C.take<AmgDev>(L);
+  };
+  Carver sz;
+  layout(sz);
+  h->amg_bytes = sz.off;
+  h->amg_block = h->mem.get(h->amg_bytes);
+  if (!h->amg_block) return SHELL_ERR_OOM;
+  Carver real;
+  real.base = (char *)h->amg_block;
+  layout(real);
+  std::vector<std::vector<float>> keep32;   // host staging kept alive until the stream synchronises
+  auto up = [&](void *dst, const void *src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  auto f32 = [&](const std::vector<double> &v) -> const float * {
+    keep32.emplace_back(v.begin(), v.end());
+    return keep32.back().data();
+  };
+  for (int l = 0; l < L; ++l) {
+    const AmgDev &D = lev[l];
+    if (l > 0) {
+      CK(up(D.a_ptr, As[l].sl_ptr.data(), 4 * As[l].sl_ptr.size()));
+      CK(up(D.a_col, As[l].sl_col.data(), 4 * As[l].sl_col.size()));
+      CK(up(D.a_val64, As[l].val.data(), 8 * As[l].val.size()));
+      CK(up(D.a_val32, f32(As[l].val), 4 * As[l].val.size()));
+      CK(up(D.rs32, f32(H.levels[l].rowsum), 4 * (size_t)D.n));
+      CK(up(D.dinv64, H.levels[l].dinv.data(), 8 * (size_t)D.n));
+      CK(up(D.dinv32, f32(H.levels[l].dinv), 4 * (size_t)D.n));
+    }
+    if (l < L - 1) {
+      CK(up(D.p_ptr, Ps[l].sl_ptr.data(), 4 * Ps[l].sl_ptr.size()));
+      CK(up(D.p_col, Ps[l].sl_col.data(), 4 * Ps[l].sl_col.size()));
+      CK(up(D.p_val64, Ps[l].val.data(), 8 * Ps[l].val.size()));
+      CK(up(D.p_val32, f32(Ps[l].val), 4 * Ps[l].val.size()));
+      CK(up(D.r_ptr, Rs[l].sl_ptr.data(), 4 * Rs[l].sl_ptr.size()));
+      CK(up(D.r_col, Rs[l].sl_col.data(), 4 * Rs[l].sl_col.size()));
+      CK(up(D.r_val64, Rs[l].val.data(), 8 * Rs[l].val.size()));
+      CK(up(D.r_val32, f32(Rs[l].val), 4 * Rs[l].val.size()));
+    }
+    CK(cudaMemsetAsync(D.b, 0, 32 * (size_t)D.n, st));
+    CK(cudaMemsetAsync(D.x, 0, 32 * (size_t)D.n, st));
+    CK(cudaMemsetAsync(D.r, 0, 32 * (size_t)D.n, st));
+    CK(cudaMemsetAsync(D.y, 0, 32 * (size_t)D.n, st));
+  }
+  CK(up(cinv64, H.coarse_inv.data(), 8 * H.coarse_inv.size()));
+  CK(up(cinv32, f32(H.coarse_inv), 4 * H.coarse_inv.size()));
+  CK(up(d_lev, lev.data(), sizeof(AmgDev) * L));
+  I.amg_levels = L;
+  I.amg_coarse_n = nc;
+  I.amg_coarse_sweeps = H.coarse_sweeps;
+  I.amg = d_lev;
+  I.amg_cinv64 = cinv64;
+  I.amg_cinv32 = cinv32;
+  CK(up(h->d_inst, &I, sizeof(Inst)));
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -800,6 +952,13 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     return (flags & 1) ? SHELL_ERR_DEGENERATE : SHELL_ERR_SINGULAR_OPERATOR;
   }
 #undef CKF
+  rc = setup_amg(h, T, opt.preconditioner);
+  if (rc != SHELL_OK) {
+    if (h->amg_block) h->mem.put(h->amg_block, h->amg_bytes);
+    h->mem.put(h->block, h->block_bytes);
+    delete h;
+    return rc;
+  }
   // ---- private batch for shell_step
   rc = batch_new(&opt, (size_t)-1, true, &h->solo);
   if (rc != SHELL_OK) {
@@ -951,6 +1110,8 @@ int shell_info(shell_handle *h, int64_t out[7]) {
   out[4] = h->nnz;
   out[5] = h->nnz_pad;
   out[6] = h->h.n_slots;
+  out[7] = h->h.amg_levels;
+  out[3] = (int64_t)(h->block_bytes + h->amg_bytes);
   return SHELL_OK;
 }
 
@@ -959,6 +1120,7 @@ int shell_destroy(shell_handle *h) {
   if (h->batch) return SHELL_ERR_BUSY;
   cudaStreamSynchronize(h->mem.st);
   batch_free(h->solo);
+  if (h->amg_block) h->mem.put(h->amg_block, h->amg_bytes);
   h->mem.put(h->block, h->block_bytes);
   cudaStreamSynchronize(h->mem.st);
   delete h;
@@ -1039,7 +1201,7 @@ int shell_batch_create(const shell_options *opt, size_t budget, shell_batch **ou
 int shell_batch_admit(shell_batch *b, shell_handle *h, int32_t *slot) {
   if (!b || !h) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
-  if (b->used + h->block_bytes > b->budget) return SHELL_ERR_BUDGET;
+  if (b->used + h->block_bytes + h->amg_bytes > b->budget) return SHELL_ERR_BUDGET;
   int k = -1;
   for (size_t q = 0; q < b->slots.size(); ++q)
     if (!b->slots[q]) {
@@ -1053,7 +1215,7 @@ int shell_batch_admit(shell_batch *b, shell_handle *h, int32_t *slot) {
   b->slots[k] = h;
   h->batch = b;
   h->slot = k;
-  b->used += h->block_bytes;
+  b->used += h->block_bytes + h->amg_bytes;
   b->dirty = true;
   if (slot) *slot = k;
   return SHELL_OK;
@@ -1066,7 +1228,7 @@ int shell_batch_retire(shell_batch *b, int32_t slot) {
   b->slots[slot] = nullptr;
   h->batch = nullptr;
   h->slot = -1;
-  b->used -= h->block_bytes;
+  b->used -= h->block_bytes + h->amg_bytes;
   b->dirty = true;
   return SHELL_OK;
 }

@@ -201,6 +201,7 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     row_ptr[i + 1] = (int32_t)cols.size();
   }
   T.nnz = (int64_t)cols.size();
+  T.row_ptr = row_ptr;
 
   // ---- SELL-32 layout
   T.n_slices = (nv + 31) / 32;

@@ -17,6 +17,7 @@ struct HostTopo {
   int n_slices = 0;
   std::vector<int32_t> sl_ptr, sl_col, diag_pos;
   int64_t nnz = 0;                   // structural nonzeros (without padding)
+  std::vector<int32_t> row_ptr;      // CSR structure of the scalar matrix (row lengths)
   int n_local = 0;
   std::vector<int32_t> asm_ptr, asm_src;
 };

@@ -41,6 +41,27 @@ struct InstStatus {
   long long total_rounds;
 };
 
+// One level of the smoothed-aggregation multigrid preconditioner (device pointers). Matrices are SELL-32:
+// A (this level's operator), P (rows of this level -> columns of the next) and R = P^T (rows of the next
+// level -> columns of this one). Level vectors are array-of-structures [n][4] in the solve precision.
+struct AmgDev {
+  int32_t n, n_next;
+  int32_t *a_ptr, *a_col;
+  float *a_val32;
+  double *a_val64;
+  float *rs32;                   // row sums (FP64 sum, rounded) for the FP32 difference-form SpMV
+  float *dinv32;
+  double *dinv64;
+  int32_t *p_ptr, *p_col;
+  float *p_val32;
+  double *p_val64;
+  int32_t *r_ptr, *r_col;
+  float *r_val32;
+  double *r_val64;
+  double omega;                  // damped-Jacobi weight
+  void *b, *x, *r, *y;
+};
+
 // Per-instance device descriptor (lives in device memory; every pointer is a device pointer).
 struct Inst {
   // sizes and parameters
@@ -111,6 +132,15 @@ struct Inst {
 
   InstStatus *status;            // one per instance
   int32_t *err_flags;            // precompute error flags (degenerate / singular)
+
+  // multigrid preconditioner (amg_levels == 0: Jacobi)
+  int32_t amg_levels;
+  int32_t amg_coarse_n;          // rows of the coarsest level
+  int32_t amg_coarse_sweeps;     // 0: dense inverse on the coarsest level, else Jacobi sweeps
+  int32_t pad1;
+  AmgDev *amg;                   // [amg_levels]
+  double *amg_cinv64;            // dense inverse of the coarsest operator [n][n]
+  float *amg_cinv32;
 };
 
 // A force tile: kForceBlock consecutive stencils of one instance.

@@ -372,10 +372,12 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
   }
 }
 
-// p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D^-1 r -> g
+// p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; then (Jacobi) u = D^-1 r -> g. With the
+// multigrid preconditioner u is read from g and the new u = B r is computed by the V-cycle afterwards.
 template <typename R>
 __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, bool first, R *x) {
   const int nv = I.nv;
+  const bool amg = I.amg_levels > 0;
   const R *dinv = Vec<R>::dinv(I);
   typename Vec<R>::G *g = Vec<R>::g(I);
   R *r = reinterpret_cast<R *>(I.r);
@@ -384,12 +386,19 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
   const R *w = reinterpret_cast<const R *>(I.w);
   ROWS_BEGIN(I, tm)
   const R di = dinv[row];
+  R uo[3];
+  if (amg) {
+    const typename Vec<R>::G gu = ldg4(g + row);
+    uo[0] = R(gu.x);
+    uo[1] = R(gu.y);
+    uo[2] = R(gu.z);
+  }
   R un[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
     const R rc = r[k];
-    const R u = di * rc;
+    const R u = amg ? uo[c] : di * rc;
     const R pc = first ? u : u + beta * p[k];
     const R sc = first ? w[k] : w[k] + beta * s[k];
     p[k] = pc;
@@ -399,8 +408,225 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
     r[k] = rn;
     un[c] = di * rn;
   }
-  g[row] = Vec<R>::mk(un[0], un[1], un[2]);
+  if (!amg) g[row] = Vec<R>::mk(un[0], un[1], un[2]);
   ROWS_END
+}
+
+// ------------------------------------------------------------------ multigrid V-cycle (preconditioner)
+// SELL-32 SpMV helpers on one level's arrays.
+template <typename R>
+struct LevelVal;
+template <>
+struct LevelVal<float> {
+  __device__ static const float *a(const AmgDev &L) { return L.a_val32; }
+  __device__ static const float *p(const AmgDev &L) { return L.p_val32; }
+  __device__ static const float *r(const AmgDev &L) { return L.r_val32; }
+  __device__ static const float *dinv(const AmgDev &L) { return L.dinv32; }
+  __device__ static const float *cinv(const Inst &I) { return I.amg_cinv32; }
+};
+template <>
+struct LevelVal<double> {
+  __device__ static const double *a(const AmgDev &L) { return L.a_val64; }
+  __device__ static const double *p(const AmgDev &L) { return L.p_val64; }
+  __device__ static const double *r(const AmgDev &L) { return L.r_val64; }
+  __device__ static const double *dinv(const AmgDev &L) { return L.dinv64; }
+  __device__ static const double *cinv(const Inst &I) { return I.amg_cinv64; }
+};
+
+// plain y_i = sum_j m_ij v_j over a SELL-32 matrix (prolongation / restriction / FP64 level operators)
+template <typename R, typename G>
+__device__ inline void sell_plain(const int32_t *sp, const int32_t *sc, const R *sv, const G *v, int row, R &ax,
+                                  R &ay, R &az) {
+  constexpr int U = 4;
+  const int s = row >> 5, lane = row & 31;
+  const int b1 = sp[s + 1];
+  ax = ay = az = R(0);
+  for (int p = sp[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    R a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? sc[q] : 0;
+      a[j] = ok ? sv[q] : R(0);
+    }
+    G t[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) t[j] = ldg4(v + c[j]);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      ax += a[j] * R(t[j].x);
+      ay += a[j] * R(t[j].y);
+      az += a[j] * R(t[j].z);
+    }
+  }
+}
+
+// level operator: FP32 in difference form (row sums), FP64 plain
+__device__ inline void level_a(const AmgDev &L, const float4 *v, int row, float &ax, float &ay, float &az) {
+  constexpr int U = 8;
+  const int s = row >> 5, lane = row & 31;
+  const int b1 = L.a_ptr[s + 1];
+  const float4 ui = v[row];
+  const float rs = L.rs32[row];
+  ax = rs * ui.x;
+  ay = rs * ui.y;
+  az = rs * ui.z;
+  for (int p = L.a_ptr[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    float a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? L.a_col[q] : row;
+      a[j] = ok ? L.a_val32[q] : 0.0f;
+    }
+    float4 t[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) t[j] = v[c[j]];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      ax += a[j] * (t[j].x - ui.x);
+      ay += a[j] * (t[j].y - ui.y);
+      az += a[j] * (t[j].z - ui.z);
+    }
+  }
+}
+__device__ inline void level_a(const AmgDev &L, const D4 *v, int row, double &ax, double &ay, double &az) {
+  sell_plain<double, D4>(L.a_ptr, L.a_col, L.a_val64, v, row, ax, ay, az);
+}
+
+#define LEVEL_ROWS_BEGIN(n, tm)                                              \
+  for (int ch = (tm).rank; ch * kBlock < (n); ch += (tm).size) {            \
+    const int row = ch * kBlock + (int)threadIdx.x;                         \
+    if (row < (n)) {
+#define LEVEL_ROWS_END \
+  }                    \
+  }
+
+// u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing, Galerkin coarse operators and a dense
+// coarsest solve; input the CG residual r (SoA), output u in g (AoS). Returns false on abort.
+template <typename R>
+__device__ bool vcycle(const Inst &I, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const int L = I.amg_levels;
+  const R *rin = reinterpret_cast<const R *>(I.r);
+  const int nv = I.nv;
+  // ---- down
+  for (int l = 0; l < L - 1; ++l) {
+    const AmgDev &A = I.amg[l];
+    G *b = reinterpret_cast<G *>(A.b);
+    G *x = reinterpret_cast<G *>(A.x);
+    G *rr = reinterpret_cast<G *>(A.r);
+    const R *dinv = LevelVal<R>::dinv(A);
+    const R om = R(A.omega);
+    LEVEL_ROWS_BEGIN(A.n, tm)
+    G bi;
+    if (l == 0) {
+      bi = Vec<R>::mk(rin[row], rin[nv + row], rin[2 * nv + row]);
+      b[row] = bi;
+    } else {
+      bi = ldg4(b + row);
+    }
+    const R d = om * dinv[row];
+    x[row] = Vec<R>::mk(d * R(bi.x), d * R(bi.y), d * R(bi.z));
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+    LEVEL_ROWS_BEGIN(A.n, tm)
+    R ax, ay, az;
+    level_a(A, x, row, ax, ay, az);
+    const G bi = ldg4(b + row);
+    rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+    G *bc = reinterpret_cast<G *>(I.amg[l + 1].b);
+    LEVEL_ROWS_BEGIN(A.n_next, tm)
+    R ax, ay, az;
+    sell_plain<R, G>(A.r_ptr, A.r_col, LevelVal<R>::r(A), rr, row, ax, ay, az);
+    bc[row] = Vec<R>::mk(ax, ay, az);
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+  }
+  // ---- coarsest
+  {
+    const AmgDev &C = I.amg[L - 1];
+    const G *b = reinterpret_cast<const G *>(C.b);
+    G *y = reinterpret_cast<G *>(C.y);
+    if (I.amg_coarse_sweeps == 0) {
+      const R *ci = LevelVal<R>::cinv(I);
+      const int n = C.n;
+      LEVEL_ROWS_BEGIN(n, tm)
+      R ax = R(0), ay = R(0), az = R(0);
+      for (int j = 0; j < n; ++j) {
+        const R a = ci[(size_t)row * n + j];
+        const G t = ldg4(b + j);
+        ax += a * R(t.x);
+        ay += a * R(t.y);
+        az += a * R(t.z);
+      }
+      y[row] = Vec<R>::mk(ax, ay, az);
+      LEVEL_ROWS_END
+      if (!team_sync(tm)) return false;
+    } else {
+      G *x = reinterpret_cast<G *>(C.x);
+      const R *dinv = LevelVal<R>::dinv(C);
+      const R om = R(C.omega);
+      LEVEL_ROWS_BEGIN(C.n, tm)
+      const G bi = ldg4(b + row);
+      const R d = om * dinv[row];
+      y[row] = Vec<R>::mk(d * R(bi.x), d * R(bi.y), d * R(bi.z));
+      LEVEL_ROWS_END
+      if (!team_sync(tm)) return false;
+      for (int sw = 1; sw < I.amg_coarse_sweeps; ++sw) {
+        G *src = (sw & 1) ? y : x;
+        G *dst = (sw & 1) ? x : y;
+        LEVEL_ROWS_BEGIN(C.n, tm)
+        R ax, ay, az;
+        level_a(C, src, row, ax, ay, az);
+        const G bi = ldg4(b + row);
+        const G xi = ldg4(src + row);
+        const R d = om * dinv[row];
+        dst[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+        LEVEL_ROWS_END
+        if (!team_sync(tm)) return false;
+      }
+      if ((I.amg_coarse_sweeps & 1) == 0) {   // the last sweep wrote x: move it to y
+        LEVEL_ROWS_BEGIN(C.n, tm)
+        y[row] = ldg4(x + row);
+        LEVEL_ROWS_END
+        if (!team_sync(tm)) return false;
+      }
+    }
+  }
+  // ---- up
+  for (int l = L - 2; l >= 0; --l) {
+    const AmgDev &A = I.amg[l];
+    const G *b = reinterpret_cast<const G *>(A.b);
+    G *x = reinterpret_cast<G *>(A.x);
+    const G *yc = reinterpret_cast<const G *>(I.amg[l + 1].y);
+    LEVEL_ROWS_BEGIN(A.n, tm)
+    R ax, ay, az;
+    sell_plain<R, G>(A.p_ptr, A.p_col, LevelVal<R>::p(A), yc, row, ax, ay, az);
+    const G xi = ldg4(x + row);
+    x[row] = Vec<R>::mk(R(xi.x) + ax, R(xi.y) + ay, R(xi.z) + az);
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+    G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
+    const R *dinv = LevelVal<R>::dinv(A);
+    const R om = R(A.omega);
+    LEVEL_ROWS_BEGIN(A.n, tm)
+    R ax, ay, az;
+    level_a(A, x, row, ax, ay, az);
+    const G bi = ldg4(b + row);
+    const G xi = ldg4(x + row);
+    const R d = om * dinv[row];
+    y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+  }
+  return true;
 }
 
 // Chronopoulos-Gear PCG iterations on A x = r0, given r (initial residual), x (initial guess) and
@@ -409,6 +635,7 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
 template <typename R>
 __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, double *rho_out) {
   if (!team_sync(tm)) return -2;
+  if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
   phase_spmv<R>(I, tm);
   if (!team_sync(tm)) return -2;
   double red[3];
@@ -422,6 +649,7 @@ __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, d
   for (int it = 1; it <= max_it; ++it) {
     phase_update<R>(I, tm, R(alpha), R(beta), first, x);
     if (!team_sync(tm)) return -2;
+    if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
     phase_spmv<R>(I, tm);
     if (!team_sync(tm)) return -2;
     team_reduce(I, tm, red);
