@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--budget-gb", type=float, default=120.0)
     return ap.parse_args()
 
 
@@ -139,13 +142,15 @@ def algorithmic_bytes(info, stats, steps):
     Per step: right-hand side 16 B per contribution slot (FP32 force + its index) + 141 B per row, commit 96 B
     per row. Per refinement round: FP64 matrix 12 B per nonzero + 216 B per row (FP64 residual, vector
     gather, inner-solve set-up, correction accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero
-    + 168 B per row (update of r, p, s, x and the gathered vector; w = A u; one gather per row).
-    Structural nonzeros are used (padding of the SELL layout is overhead, not algorithmic).
+    + 168 B per row (update of r, p, s, x and the gathered vector; w = A u; one gather per row), plus one
+    multigrid V-cycle per iteration and per round when the instance uses the multigrid preconditioner
+    (``vcycle_bytes`` from shell_info). Structural nonzeros are used (SELL padding is overhead).
     """
     V, nnz, slots = info["n_verts"], info["nnz"], info["n_slots"]
+    vc = float(info.get("vcycle_bytes", 0))
     per_step = 16.0 * slots + (141.0 + 96.0) * V
-    per_round = 12.0 * nnz + 216.0 * V
-    per_iter = 8.0 * nnz + 168.0 * V
+    per_round = 12.0 * nnz + 216.0 * V + vc
+    per_iter = 8.0 * nnz + 168.0 * V + vc
     return steps * per_step + stats["total_refine_rounds"] * per_round + stats["total_pcg_iterations"] * per_iter
 
 
@@ -164,6 +169,32 @@ def time_oracle(scs, budget_s, max_steps=5):
         if t_step >= budget_s:
             break
     return done_vs / t_step, f"first {n_inst} instances of the workload, {steps_each} steps each, step time only", t_step
+
+
+def serve(args, gb, torch, dev, rank, world):
+    """Continuous-batching serving workload: Poisson(200/s) arrivals of jittered-grid requests (1k-250k
+    vertices, random model, 50-500 steps), admitted by an HBM budget, stepped together; bounded wall time."""
+    import shellgen as sg
+    from paper_2502_10872_gb300.serving import Request, Server
+    torch.cuda.set_stream(torch.cuda.Stream())
+    arrivals = sg.serving_requests(args.serve_requests, rate_hz=200.0, seed=args.seed + 1000 * rank)
+    reqs = [Request(k, t, sc, sc.steps) for k, (t, sc) in enumerate(arrivals)]
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), precision="fp32_refine")
+    with Clocks(dev) as clk:
+        rep = srv.run(reqs, max_wall_s=args.serve_seconds)
+    srv.close()
+    summ = rep.summary()
+    peak, peak_kind = load_peaks()
+    line = {"metric": METRIC, "value": summ["vertex_steps_per_s"], "unit": "vertex-steps/s", "n_gpus": world,
+            "steps": summ["batch_steps"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving", "arrivals": "Poisson 200/s", "requests_offered": len(reqs),
+                       "vertices": "log-uniform 1k-250k (jittered grids)", "steps": "uniform 50-500",
+                       "budget_gb": args.budget_gb, "wall_limit_s": args.serve_seconds, "seed": args.seed},
+            "latency_ms": {"p50": summ["step_ms_p50"], "p99": summ["step_ms_p99"]},
+            "serving": summ, "clocks": clk.summary(), "peak_hbm_gbs": peak, "peak_kind": peak_kind}
+    if rank == 0:
+        emit(line)
 
 
 def emit(obj):
@@ -206,6 +237,8 @@ def main():
     else:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
+    if args.workload == "serving":
+        return serve(args, gb, torch, dev, rank, world)
     # a non-default stream, so the per-step launches can be captured into a CUDA graph
     torch.cuda.set_stream(torch.cuda.Stream())
     gb.load_library()
@@ -225,7 +258,12 @@ def main():
             gb.shell_batch_admit(b, h)
         return b, hs
 
-    def timed(b, K, W, profile):
+    tuned = {}
+
+    def timed(b, K, W, profile, tune_key=None):
+        if tune_key is not None:
+            # the autotuner runs real steps (part of the untimed warm-up); results do not depend on it
+            tuned[tune_key] = gb.shell_batch_autotune(b, 2)
         gb.shell_batch_step(b, W)
         barrier()
         gb.shell_batch_set_profiling(b, profile)
@@ -242,7 +280,7 @@ def main():
     # ---- FP32 + refinement (headline)
     b32, h32 = make_batch("fp32_refine")
     with Clocks(dev) as clk:
-        stats32, times32, kern32, wall32 = timed(b32, K, W, profile=True)
+        stats32, times32, kern32, wall32 = timed(b32, K, W, profile=True, tune_key="fp32_refine")
     dev_s = float(np.sum(times32)) / 1000.0
     t_rank = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -265,7 +303,7 @@ def main():
     acc = None
     if not args.no_fp64:
         b64, h64 = make_batch("fp64")
-        stats64, times64, _, _ = timed(b64, K, W, profile=False)
+        stats64, times64, _, _ = timed(b64, K, W, profile=False, tune_key="fp64")
         fp64_value = V_total * K / (float(np.sum(times64)) / 1000.0)
         worst = 0.0
         for k, sc in enumerate(scs):
@@ -276,7 +314,7 @@ def main():
         fp64 = {"value": fp64_value, "unit": "vertex-steps/s", "p50_ms": float(np.percentile(times64, 50)),
                 "p99_ms": float(np.percentile(times64, 99)),
                 "pcg_iterations_per_step": float(np.mean([s["total_pcg_iterations"] for s in stats64.values()]) / K)}
-        acc = {"max_rel_x_fp32r_vs_fp64": worst, "steps": W + K}
+        acc = {"max_rel_x_fp32r_vs_fp64": worst, "steps": W + K + tuned["fp32_refine"]["steps"]}
         gb.shell_batch_destroy(b64)
         del h64
 
@@ -322,6 +360,7 @@ def main():
                    "l2": "inputs larger than L2 (batch working set > 129 MB)", "seed": args.seed,
                    "parallelism": f"instances per rank, {world} rank(s)"},
         "latency_ms": {"p50": p50, "p99": p99},
+        "autotune": tuned,
         "fp64": fp64, "accuracy": acc,
         "solver": {"mean_inner_iterations_per_step": float(np.mean(iters)),
                    "max_inner_iterations_per_step": float(np.max(iters)),

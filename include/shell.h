@@ -201,8 +201,10 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
 
 /* Sizes: out[0] vertices, out[1] triangles, out[2] bending stencils, out[3] bytes of device memory the handle
  * holds, out[4] structural nonzeros of the scalar matrix, out[5] stored (SELL-padded) nonzeros, out[6]
- * force contribution slots, out[7] multigrid levels (0 = Jacobi preconditioner). */
-int shell_info(shell_handle *h, int64_t out[8]);
+ * force contribution slots, out[7] multigrid levels (0 = Jacobi preconditioner), out[8] algorithmic bytes
+ * of one FP32 V-cycle (16 B per level-operator nonzero, 8 B per prolongation / restriction nonzero, 200 B
+ * per level row, 4 B per entry of the dense coarsest inverse; 0 without multigrid). */
+int shell_info(shell_handle *h, int64_t out[9]);
 
 int shell_destroy(shell_handle *h);
 const char *shell_strerror(int code);
@@ -239,6 +241,12 @@ int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
  * then gives out_ms[0] = summed force-kernel time and out_ms[1] = summed solve-kernel time of the last
  * call, in milliseconds. */
 int shell_batch_set_profiling(shell_batch *b, int32_t on);
+/* Autotune the persistent solve launch of this batch: tries 3 occupancies (CTAs per SM: 1, half, the
+ * maximum) x 3 CTA shares for large instances (x0.5, x1, x2), steps_per_trial real (committed) steps each,
+ * and keeps the fastest by device time. A batch's results do not depend on the launch shape, so tuning
+ * changes only speed. out_ms: NULL or [9] mean step time of each trial (-1 if skipped); out_choice: NULL or
+ * [2] = {CTAs per SM, share x 100}. */
+int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice);
 int shell_batch_kernel_times(shell_batch *b, double out_ms[2]);
 int shell_batch_destroy(shell_batch *b);
 

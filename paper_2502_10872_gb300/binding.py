@@ -39,6 +39,7 @@ EXPORTS = (
     "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
+    "shell_batch_autotune",
     "shell_batch_destroy",
 )
 
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_step_times": (C.c_int, [P, P, C.c_int32]),
         "shell_batch_set_profiling": (C.c_int, [P, C.c_int32]),
         "shell_batch_kernel_times": (C.c_int, [P, P]),
+        "shell_batch_autotune": (C.c_int, [P, C.c_int32, P, P]),
         "shell_batch_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
@@ -351,10 +353,11 @@ def shell_set_state_device(h: Handle, x_dev=None, v_dev=None):
 
 
 def shell_info(h: Handle) -> dict:
-    out = np.zeros(8, np.int64)
+    out = np.zeros(9, np.int64)
     _check(load_library().shell_info(h.ptr, out.ctypes.data), "shell_info")
     return {"n_verts": int(out[0]), "n_tris": int(out[1]), "n_stencils": int(out[2]), "device_bytes": int(out[3]),
-            "nnz": int(out[4]), "nnz_stored": int(out[5]), "n_slots": int(out[6]), "amg_levels": int(out[7])}
+            "nnz": int(out[4]), "nnz_stored": int(out[5]), "n_slots": int(out[6]), "amg_levels": int(out[7]),
+            "vcycle_bytes": int(out[8])}
 
 
 def shell_destroy(h: Handle):
@@ -444,6 +447,16 @@ def shell_batch_kernel_times(b: Batch) -> np.ndarray:
     out = np.zeros(2, np.float64)
     _check(load_library().shell_batch_kernel_times(b.ptr, out.ctypes.data), "shell_batch_kernel_times")
     return out
+
+
+def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:
+    """Pick the fastest launch shape of the batch's solve kernel on real steps (see include/shell.h)."""
+    ms = np.zeros(9, np.float64)
+    choice = np.zeros(2, np.int32)
+    _check(load_library().shell_batch_autotune(b.ptr, int(steps_per_trial), ms.ctypes.data, choice.ctypes.data),
+           "shell_batch_autotune")
+    return {"trial_ms": ms.tolist(), "ctas_per_sm": int(choice[0]), "share_scale": choice[1] / 100.0,
+            "steps": int(np.sum(ms >= 0)) * int(steps_per_trial)}
 
 
 def shell_batch_destroy(b: Batch):

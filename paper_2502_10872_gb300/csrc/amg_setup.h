@@ -35,7 +35,7 @@ struct HostAmg {
 
 // Builds the hierarchy of the SPD matrix A (CSR, diagonal present). Rows whose only entry is the diagonal
 // (pinned vertices) are left out of the coarse spaces: the smoother solves them exactly.
-void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_max = 192, double theta = 0.08);
+void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_max = 48, double theta = 0.08);
 
 HostSell to_sell(const HostCsr &M);
 

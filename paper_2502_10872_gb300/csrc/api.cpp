@@ -106,6 +106,7 @@ struct shell_handle {
   Tile *d_tiles = nullptr;       // the same tiles on the device (inst index 0 = d_inst)
   void *amg_block = nullptr;     // multigrid hierarchy (device), if any
   size_t amg_bytes = 0;
+  int64_t vcycle_bytes = 0;      // algorithmic bytes of one FP32 V-cycle
   double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
   double sched_est = 64.0;       // estimate the current schedule was planned with
   int64_t nnz = 0, nnz_pad = 0;
@@ -138,6 +139,9 @@ struct shell_batch {
   cudaGraphExec_t gexec = nullptr;
   bool graph_tried = false;
   bool profiling = false;
+  int occ = 0;                 // CTAs per SM of the solve launch (0 = the occupancy maximum)
+  bool cluster_off = false;    // set if a cluster launch was refused
+  double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
   double kern_ms[2] = {0.0, 0.0};
 };
@@ -147,6 +151,11 @@ namespace {
 int blocks_per_sm_cached(int prec) {
   static int n[3] = {-1, -1, -1};
   if (n[prec] < 0) n[prec] = std::max(1, solve_blocks_per_sm(prec));
+  return n[prec];
+}
+int max_clusters_cached(int prec) {
+  static int n[3] = {-1, -1, -1};
+  if (n[prec] < 0) n[prec] = std::max(0, solve_max_clusters(prec, kCluster));
   return n[prec];
 }
 int num_sms() {
@@ -194,34 +203,47 @@ int rebuild_tables(shell_batch *b) {
   bool any64 = false, any32 = false;
   for (int k = 0; k < n; ++k) (b->slots[b->active[k]]->h.precision == SHELL_FP64 ? any64 : any32) = true;
   b->prec = (any64 && any32) ? 0 : (any64 ? 1 : 2);
-  const int G = num_sms() * blocks_per_sm_cached(b->prec);
+  const int occ_max = blocks_per_sm_cached(b->prec);
+  const int occ = (b->occ > 0 && b->occ < occ_max) ? b->occ : occ_max;
+  // thread-block clusters: teams that are whole clusters synchronise with the hardware cluster barrier
+  const int CS = b->cluster_off ? 0 : (max_clusters_cached(b->prec) > 0 ? kCluster : 0);
+  int G = num_sms() * occ;
+  if (CS) G = std::min(G, max_clusters_cached(b->prec) * CS) / CS * CS;
   std::vector<double> work(n);
   double total = 0.0;
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
-    work[k] = (double)h->nv * std::max(1.0, h->est_iters);
+    work[k] = (double)h->nv * std::max(1.0, h->est_iters) * (h->h.amg_levels > 0 ? 6.0 : 1.0);
     h->sched_est = h->est_iters;
     total += work[k];
   }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
-  const double share = total / G;
+  const double share = total / G / b->share_scale;
   std::vector<int> team_size, team_of(n, -1);
   std::vector<std::vector<int>> team_inst;
   int used = 0;
-  // big instances get their own multi-CTA team sized by their share of the work
+  // big instances get their own multi-CTA team sized by their share of the work (whole clusters when the
+  // launch uses clusters; those teams come first, so they start on cluster boundaries)
   for (int k : order) {
     const shell_handle *h = b->slots[b->active[k]];
     int want = (int)std::floor(work[k] / share);
-    want = std::min(want, h->h.n_chunks);
-    if (want < 2) break;
+    if (CS) {
+      if (want < CS / 2) break;
+      want = std::max(1, (int)std::lround((double)want / CS)) * CS;
+      want = std::min(want, ((h->h.n_chunks + CS - 1) / CS) * CS);
+    } else {
+      want = std::min(want, h->h.n_chunks);
+      if (want < 2) break;
+    }
     int left_small = 0;
     for (int q = 0; q < n; ++q)
       if (team_of[q] < 0 && q != k) ++left_small;
-    const int room = G - used - (left_small > 0 ? 1 : 0);
+    int room = G - used - (left_small > 0 ? 1 : 0);
+    if (CS) room = room / CS * CS;
     want = std::min(want, room);
-    if (want < 2) break;
+    if (want < (CS ? CS : 2)) break;
     team_of[k] = (int)team_size.size();
     team_size.push_back(want);
     team_inst.push_back({k});
@@ -248,7 +270,8 @@ int rebuild_tables(shell_batch *b) {
     used += n1;
   }
   const int n_teams = (int)team_size.size();
-  std::vector<int32_t> cta_team(used), cta_rank(used), tsize(n_teams), tptr(n_teams + 1, 0), tlist;
+  const int grid = CS ? (used + CS - 1) / CS * CS : used;   // whole clusters; spare CTAs return at once
+  std::vector<int32_t> cta_team(grid, -1), cta_rank(grid, 0), tsize(n_teams), tptr(n_teams + 1, 0), tlist;
   int c = 0;
   for (int t = 0; t < n_teams; ++t) {
     tsize[t] = team_size[t];
@@ -260,7 +283,7 @@ int rebuild_tables(shell_batch *b) {
     for (int k : team_inst[t]) tlist.push_back(k);
     tptr[t + 1] = (int32_t)tlist.size();
   }
-  b->grid = used;
+  b->grid = grid;
   b->n_teams = n_teams;
   // ---- one device table block
   Carver cv;
@@ -268,13 +291,14 @@ int rebuild_tables(shell_batch *b) {
     b->d_insts = C.take<Inst>(n);
     b->d_tiles64 = C.take<Tile>(t64.size());
     b->d_tiles32 = C.take<Tile>(t32.size());
-    b->sched.cta_team = C.take<int32_t>(used);
-    b->sched.cta_rank = C.take<int32_t>(used);
+    b->sched.cta_team = C.take<int32_t>(grid);
+    b->sched.cta_rank = C.take<int32_t>(grid);
     b->sched.team_size = C.take<int32_t>(n_teams);
     b->sched.team_ptr = C.take<int32_t>(n_teams + 1);
     b->sched.team_list = C.take<int32_t>(tlist.size());
     b->sched.bar = C.take<unsigned int>((size_t)kBarWords * n_teams);
     b->sched.abort_flag = C.take<int32_t>(1);
+    b->sched.cluster_ok = C.take<int32_t>(grid / (CS ? CS : 1) + 1);
     b->d_status_out = C.take<InstStatus>(n);
     b->d_abort_out = C.take<int32_t>(1);
   };
@@ -291,13 +315,14 @@ int rebuild_tables(shell_batch *b) {
   Carver real;
   real.base = (char *)b->tbl;
   layout(real);
-  b->sched.n_ctas = used;
+  b->sched.n_ctas = grid;
+  b->sched.cluster = CS;
   cudaStream_t st = b->mem.st;
   CK(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
   if (!t64.empty()) CK(cudaMemcpyAsync(b->d_tiles64, t64.data(), sizeof(Tile) * t64.size(), cudaMemcpyHostToDevice, st));
   if (!t32.empty()) CK(cudaMemcpyAsync(b->d_tiles32, t32.data(), sizeof(Tile) * t32.size(), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(b->sched.cta_team, cta_team.data(), 4 * used, cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(b->sched.cta_rank, cta_rank.data(), 4 * used, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.cta_team, cta_team.data(), 4 * grid, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(b->sched.cta_rank, cta_rank.data(), 4 * grid, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_ptr, tptr.data(), 4 * (n_teams + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_list, tlist.data(), 4 * tlist.size(), cudaMemcpyHostToDevice, st));
@@ -310,11 +335,24 @@ int rebuild_tables(shell_batch *b) {
   return SHELL_OK;
 }
 
+// the solve launch; if the driver refuses the cluster launch, fall back to plain global team barriers (the
+// team layout stays valid: whole-cluster teams become flat global-barrier teams)
+cudaError_t solve_launch(shell_batch *b, cudaStream_t st) {
+  cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, st);
+  if (e != cudaSuccess && b->sched.cluster > 0) {
+    cudaGetLastError();
+    b->cluster_off = true;
+    b->sched.cluster = 0;
+    e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, st);
+  }
+  return e;
+}
+
 int launch_step(shell_batch *b) {
   cudaStream_t st = b->mem.st;
   CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
   CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
-  CK(launch_solve(b->d_insts, b->sched, b->grid, b->prec, st));
+  CK(solve_launch(b, st));
   return SHELL_OK;
 }
 
@@ -380,7 +418,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
       CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
       CK(cudaEventRecord(b->pev[3 * s + 1], st));
-      CK(launch_solve(b->d_insts, b->sched, b->grid, b->prec, st));
+      CK(solve_launch(b, st));
       CK(cudaEventRecord(b->pev[3 * s + 2], st));
     } else if (b->gexec) {
       CK(cudaGraphLaunch(b->gexec, st));
@@ -555,6 +593,15 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
   build_amg(A, &H);
   const int L = (int)H.levels.size();
   if (L < 2) return SHELL_OK;
+  // one V(1,1) cycle reads every level operator twice, P and R once (8 B per FP32 nonzero with its
+  // column), about 200 B per row of level vectors, and the dense coarsest inverse once
+  h->vcycle_bytes = 0;
+  for (int l = 0; l < L; ++l) {
+    const HostAmgLevel &V = H.levels[l];
+    h->vcycle_bytes += 16 * (int64_t)V.A.val.size() + 200 * (int64_t)V.A.n;
+    if (l < L - 1) h->vcycle_bytes += 8 * (int64_t)(V.P.val.size() + V.R.val.size());
+  }
+  h->vcycle_bytes += 4 * (int64_t)H.coarse_inv.size();
   std::vector<HostSell> As(L), Ps(L), Rs(L);
   for (int l = 0; l < L; ++l) {
     if (l > 0) As[l] = to_sell(H.levels[l].A);
@@ -1101,7 +1148,7 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
   return SHELL_OK;
 }
 
-int shell_info(shell_handle *h, int64_t out[7]) {
+int shell_info(shell_handle *h, int64_t out[9]) {
   if (!h || !out) return SHELL_ERR_INVALID_ARG;
   out[0] = h->nv;
   out[1] = h->nt;
@@ -1111,6 +1158,7 @@ int shell_info(shell_handle *h, int64_t out[7]) {
   out[5] = h->nnz_pad;
   out[6] = h->h.n_slots;
   out[7] = h->h.amg_levels;
+  out[8] = h->vcycle_bytes;
   out[3] = (int64_t)(h->block_bytes + h->amg_bytes);
   return SHELL_OK;
 }
@@ -1244,6 +1292,51 @@ int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n) {
   if (!b || !out_ms || n < 0) return SHELL_ERR_INVALID_ARG;
   for (int k = 0; k < n && k < (int)b->step_ms.size(); ++k) out_ms[k] = b->step_ms[k];
   return std::min<int>(n, (int)b->step_ms.size());
+}
+
+// Autotuner: the results of a batch do not depend on its launch shape (every reduction has a fixed order
+// independent of the team layout), so candidate shapes are tried on real, committed steps and timed with
+// CUDA events; the fastest is kept.
+int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice) {
+  if (!b || steps_per_trial < 1) return SHELL_ERR_INVALID_ARG;
+  if (b->dirty) {
+    int rc = rebuild_tables(b);
+    if (rc != SHELL_OK) return rc;
+  }
+  if (b->n_active == 0) return SHELL_OK;
+  const int occ_max = blocks_per_sm_cached(b->prec);
+  const int occs[3] = {1, std::max(1, occ_max / 2), occ_max};
+  const double scales[3] = {0.5, 1.0, 2.0};
+  double best = 1e300;
+  int best_k = 0;
+  for (int k = 0; k < 9; ++k) {
+    const int oi = k / 3, si = k % 3;
+    if (oi == 1 && occs[1] == occs[0]) {
+      if (out_ms) out_ms[k] = -1.0;
+      continue;
+    }
+    b->occ = occs[oi];
+    b->share_scale = scales[si];
+    b->dirty = true;
+    int rc = batch_step(b, steps_per_trial, nullptr);
+    if (rc != SHELL_OK) return rc;
+    double ms = 0.0;
+    for (float t : b->step_ms) ms += t;
+    ms /= std::max<size_t>(1, b->step_ms.size());
+    if (out_ms) out_ms[k] = ms;
+    if (ms < best) {
+      best = ms;
+      best_k = k;
+    }
+  }
+  b->occ = occs[best_k / 3];
+  b->share_scale = scales[best_k % 3];
+  b->dirty = true;
+  if (out_choice) {
+    out_choice[0] = b->occ;
+    out_choice[1] = (int32_t)std::lround(b->share_scale * 100.0);
+  }
+  return SHELL_OK;
 }
 
 int shell_batch_set_profiling(shell_batch *b, int32_t on) {

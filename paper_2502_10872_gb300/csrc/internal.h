@@ -153,12 +153,18 @@ struct Tile {
 
 // Persistent-solve schedule: CTA b belongs to team cta_team[b] with rank cta_rank[b]; team t has
 // team_size[t] CTAs and processes instances team_list[team_ptr[t] .. team_ptr[t+1]) in order.
+// With cluster > 0 the launch uses thread-block clusters of that many CTAs; a team whose size is a multiple
+// of the cluster size starts on a cluster boundary and synchronises with the hardware cluster barrier
+// (one cluster), or hierarchically (cluster barrier, then a bounded global barrier between the clusters'
+// leader CTAs, then the cluster barrier again). Every other multi-CTA team uses the global barrier.
 struct Sched {
   int32_t *cta_team, *cta_rank;
   int32_t *team_size, *team_ptr, *team_list;
   unsigned int *bar;     // [n_teams][kBarWords] barrier words
   int32_t *abort_flag;   // set when a bounded wait gives up
+  int32_t *cluster_ok;   // [n_ctas / cluster] per-cluster barrier verdict (hierarchical teams)
   int32_t n_ctas;
+  int32_t cluster;       // CTAs per cluster of the launch, 0 = no clusters
 };
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)
@@ -179,6 +185,8 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
 cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
                            cudaStream_t st);
 int solve_blocks_per_sm(int prec);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
+int solve_max_clusters(int prec, int cluster);   // co-resident clusters of the solve kernel, 0 if unsupported
+constexpr int kCluster = 8;                      // cluster size of the batched solve launch (portable)
 int static_max_ctas();
 cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
                                int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st);

@@ -48,48 +48,77 @@ struct Team {
   int team, rank, size;
   unsigned int *bar;
   int *abort_flag;
-  int bank;   // partials are double-buffered: reduction k writes bank k % 2
+  int bank;     // partials are double-buffered: reduction k writes bank k % 2
+  int mode;     // 0: one CTA; 1: global barrier; 2: one whole cluster; 3: several whole clusters
+  int cluster;  // CTAs per cluster
+  int *cluster_ok;
 };
+
+__device__ inline void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ inline unsigned int cluster_ctarank() {
+  unsigned int r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
 
 __device__ inline double *part_of(const Inst &I, const Team &tm, int ch) {
   return I.part + 4 * ((size_t)tm.bank * I.n_chunks + ch);
 }
 
-// Team barrier. Returns false if the barrier was abandoned (timeout or abort raised by another CTA).
+// Bounded global-memory barrier among `parties` arrivals on the team's words (thread 0 of the caller only).
+// Returns 0 if it gave up (timeout, or abort raised elsewhere).
+__device__ int global_arrive_wait(const Team &tm, unsigned int parties) {
+  unsigned int *count = tm.bar;
+  unsigned int *gen = tm.bar + kBarWords / 2;
+  const unsigned int g = ld_acquire(gen);
+  __threadfence();
+  const unsigned int arrived = atomicAdd(count, 1u);
+  if (arrived == parties - 1u) {
+    atomicExch(count, 0u);
+    __threadfence();
+    atomicAdd(gen, 1u);
+  } else {
+    const unsigned long long t0 = gtimer();
+    const unsigned long long limit = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
+    while (ld_acquire(gen) == g) {
+      if (ld_volatile_i(tm.abort_flag)) return 0;
+      if (gtimer() - t0 > limit) {
+        atomicExch(tm.abort_flag, 1);
+        return 0;
+      }
+      __nanosleep(32);
+    }
+  }
+  __threadfence();
+  return 1;
+}
+
+// Team barrier. Returns false if the barrier was abandoned (timeout or abort raised by another CTA); every
+// CTA of a team, and of a cluster, gets the same verdict.
 __device__ bool team_sync(const Team &tm) {
   __shared__ int s_ok;
   __syncthreads();
-  if (tm.size == 1) return true;
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    unsigned int *count = tm.bar;
-    unsigned int *gen = tm.bar + kBarWords / 2;
-    const unsigned int g = ld_acquire(gen);
-    __threadfence();
-    const unsigned int arrived = atomicAdd(count, 1u);
-    if (arrived == (unsigned int)tm.size - 1u) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      const unsigned long long t0 = gtimer();
-      const unsigned long long limit = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
-      while (ld_acquire(gen) == g) {
-        if (ld_volatile_i(tm.abort_flag)) {
-          ok = 0;
-          break;
-        }
-        if (gtimer() - t0 > limit) {
-          atomicExch(tm.abort_flag, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
+  if (tm.mode == 0) return true;
+  if (tm.mode == 2) {            // the team is one cluster: hardware barrier, cannot time out
+    cluster_barrier();
+    return true;
   }
+  if (tm.mode == 3) {            // several clusters: cluster barrier, leaders meet globally, cluster barrier
+    cluster_barrier();
+    const unsigned int crank = cluster_ctarank();
+    int *flag = tm.cluster_ok + (blockIdx.x / tm.cluster);
+    if (crank == 0 && threadIdx.x == 0) {
+      const int ok = global_arrive_wait(tm, (unsigned int)(tm.size / tm.cluster));
+      *((volatile int *)flag) = ok;
+    }
+    cluster_barrier();
+    if (threadIdx.x == 0) s_ok = *((volatile int *)flag);
+    __syncthreads();
+    return s_ok != 0;
+  }
+  if (threadIdx.x == 0) s_ok = global_arrive_wait(tm, (unsigned int)tm.size);
   __syncthreads();
   return s_ok != 0;
 }
@@ -192,7 +221,9 @@ __device__ inline float4 ldg4(const float4 *p) { return *p; }
 // y = A g for one row (SELL-32)
 // g is written by other CTAs during the launch: it must not be read through the non-coherent path, so it
 // carries no __restrict__ / const-restrict qualification. Both forms issue the column, value and gather
-// loads of several nonzeros before consuming them (memory-level parallelism per thread).
+// loads of several nonzeros before consuming them (memory-level parallelism per thread). Matrix columns
+// and values are read once per product and loaded with the streaming hint (evict first), so they do not
+// push the gathered vector, which every row re-reads, out of L1 and L2.
 //
 // FP64 (refinement residual, FP64 CG): y_i = sum_j a_ij g_j.
 __device__ inline void spmv_row(const Inst &I, const double *__restrict__ val, const D4 *g, int row, double &ax,
@@ -208,8 +239,8 @@ __device__ inline void spmv_row(const Inst &I, const double *__restrict__ val, c
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? I.sl_col[q] : row;
-      a[j] = ok ? val[q] : 0.0;
+      c[j] = ok ? __ldcs(I.sl_col + q) : row;
+      a[j] = ok ? __ldcs(val + q) : 0.0;
     }
     D4 v[U];
 #pragma unroll
@@ -245,8 +276,8 @@ __device__ inline void spmv_row(const Inst &I, const float *__restrict__ val, co
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? I.sl_col[q] : row;
-      a[j] = ok ? val[q] : 0.0f;
+      c[j] = ok ? __ldcs(I.sl_col + q) : row;
+      a[j] = ok ? __ldcs(val + q) : 0.0f;
     }
     float4 v[U];
 #pragma unroll
@@ -448,8 +479,8 @@ __device__ inline void sell_plain(const int32_t *sp, const int32_t *sc, const R 
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? sc[q] : 0;
-      a[j] = ok ? sv[q] : R(0);
+      c[j] = ok ? __ldcs(sc + q) : 0;
+      a[j] = ok ? __ldcs(sv + q) : R(0);
     }
     G t[U];
 #pragma unroll
@@ -480,8 +511,8 @@ __device__ inline void level_a(const AmgDev &L, const float4 *v, int row, float 
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? L.a_col[q] : row;
-      a[j] = ok ? L.a_val32[q] : 0.0f;
+      c[j] = ok ? __ldcs(L.a_col + q) : row;
+      a[j] = ok ? __ldcs(L.a_val32 + q) : 0.0f;
     }
     float4 t[U];
 #pragma unroll
@@ -813,6 +844,14 @@ __global__ void __launch_bounds__(kBlock, PREC == 2 ? 3 : 2) k_solve(const Inst 
   tm.bar = sch.bar + kBarWords * tm.team;
   tm.abort_flag = sch.abort_flag;
   tm.bank = 0;
+  tm.cluster = sch.cluster;
+  tm.cluster_ok = sch.cluster_ok;
+  if (tm.size == 1)
+    tm.mode = 0;
+  else if (sch.cluster > 0 && tm.size % sch.cluster == 0)
+    tm.mode = (tm.size == sch.cluster) ? 2 : 3;
+  else
+    tm.mode = 1;
   for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
     const Inst &I = insts[sch.team_list[q]];
     if (I.status->err != SHELL_OK) continue;
@@ -846,14 +885,48 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int 
   cfg.blockDim = dim3(kBlock);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
+  int na = 1;
+  if (sched.cluster > 0) {
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = sched.cluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    na = 2;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   if (prec == 1) return cudaLaunchKernelEx(&cfg, k_solve<1>, d_insts, sched);
   if (prec == 2) return cudaLaunchKernelEx(&cfg, k_solve<2>, d_insts, sched);
   return cudaLaunchKernelEx(&cfg, k_solve<0>, d_insts, sched);
+}
+
+int solve_max_clusters(int prec, int cluster) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(kBlock);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e;
+  if (prec == 1)
+    e = cudaOccupancyMaxActiveClusters(&n, k_solve<1>, &cfg);
+  else if (prec == 2)
+    e = cudaOccupancyMaxActiveClusters(&n, k_solve<2>, &cfg);
+  else
+    e = cudaOccupancyMaxActiveClusters(&n, k_solve<0>, &cfg);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 // ---------------------------------------------------------------- step without device allocation
@@ -910,6 +983,8 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   int32_t *abort_out = sc.abort_flag + 1;
   InstStatus *status_out = reinterpret_cast<InstStatus *>(base + kStaticStatus);
   sc.n_ctas = team_ctas;
+  sc.cluster = 0;
+  sc.cluster_ok = nullptr;
   static thread_local int32_t host_tab[2 * kStaticMaxCtas + 4];
   for (int c = 0; c < team_ctas; ++c) {
     host_tab[c] = 0;
