@@ -66,6 +66,28 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def solve_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("kernels_solve.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2502_10872_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload_name):
+    """DRAM bytes per solve launch from the committed ncu summary, if it was taken on the current source of
+    the solve kernel and this workload (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_solve_traffic.txt")
+    try:
+        kv = dict(line.split(None, 1) for line in open(path) if line.strip() and not line.startswith("#"))
+    except Exception:
+        return None
+    if kv.get("source_sha1", "").strip() != solve_source_hash() or kv.get("workload", "").strip() != workload_name:
+        return None
+    return float(kv["traffic_bytes_per_launch"])
+
+
 def workload(name, seed, rank):
     import shellgen as sg
     if name == "batch256":
@@ -366,7 +388,7 @@ def main():
                    "max_inner_iterations_per_step": float(np.max(iters)),
                    "mean_refine_rounds_per_step": float(np.mean(rounds))},
         "roofline": {"kernel": "k_solve", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": measured_traffic(args.workload), "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo / K, "mean_launch_ms": kern32[1] / K,
                      "force_kernel_ms_per_step": kern32[0] / K},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),

@@ -146,6 +146,9 @@ typedef struct shell_step_stats {
   int64_t total_pcg_iterations;/* summed over the call's steps */
   double rel_residual;         /* ||b - A v'|| / ||b|| of the last committed step (recursive in FP64) */
   int64_t total_refine_rounds; /* summed over the call's steps */
+  double last_solve_us;        /* device time of the last step's solve of this instance (rhs to commit) */
+  int32_t team_ctas;           /* CTAs of the persistent launch that worked on this instance */
+  int32_t pad;
 } shell_step_stats;
 
 /* ------------------------------------------------------------------------------------------ handle */
@@ -241,11 +244,12 @@ int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
  * then gives out_ms[0] = summed force-kernel time and out_ms[1] = summed solve-kernel time of the last
  * call, in milliseconds. */
 int shell_batch_set_profiling(shell_batch *b, int32_t on);
-/* Autotune the persistent solve launch of this batch: tries 3 occupancies (CTAs per SM: 1, half, the
- * maximum) x 3 CTA shares for large instances (x0.5, x1, x2), steps_per_trial real (committed) steps each,
- * and keeps the fastest by device time. A batch's results do not depend on the launch shape, so tuning
- * changes only speed. out_ms: NULL or [9] mean step time of each trial (-1 if skipped); out_choice: NULL or
- * [2] = {CTAs per SM, share x 100}. */
+/* Autotune the persistent solve launch of this batch: flat teams (any size, global barriers, cooperative
+ * launch) with 3 occupancies (CTAs per SM: 1, half, the maximum) x 3 CTA shares for large instances (x0.5,
+ * x1, x2), and one-cluster teams (8-CTA thread-block clusters, hardware cluster barrier) with the 3 shares;
+ * steps_per_trial real (committed) steps each; keeps the fastest by device time. A batch's results do not
+ * depend on the launch shape, so tuning changes only speed. out_ms: NULL or [12] mean step time of each trial
+ * (-1 if skipped, -2 if it ran but the cluster launch was refused); out_choice: NULL or [3] = {CTAs per SM, share x 100, 1 if clusters}. */
 int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice);
 int shell_batch_kernel_times(shell_batch *b, double out_ms[2]);
 int shell_batch_destroy(shell_batch *b);

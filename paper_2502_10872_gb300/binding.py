@@ -85,7 +85,8 @@ class shell_options(C.Structure):
 class shell_step_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("pcg_iterations", C.c_int32), ("refine_rounds", C.c_int32),
                 ("status", C.c_int32), ("total_pcg_iterations", C.c_int64), ("rel_residual", C.c_double),
-                ("total_refine_rounds", C.c_int64)]
+                ("total_refine_rounds", C.c_int64), ("last_solve_us", C.c_double), ("team_ctas", C.c_int32),
+                ("pad", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -451,12 +452,13 @@ def shell_batch_kernel_times(b: Batch) -> np.ndarray:
 
 def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:
     """Pick the fastest launch shape of the batch's solve kernel on real steps (see include/shell.h)."""
-    ms = np.zeros(9, np.float64)
-    choice = np.zeros(2, np.int32)
+    ms = np.zeros(12, np.float64)
+    choice = np.zeros(3, np.int32)
     _check(load_library().shell_batch_autotune(b.ptr, int(steps_per_trial), ms.ctypes.data, choice.ctypes.data),
            "shell_batch_autotune")
+    ran = int(np.sum(ms != -1.0))     # -1: skipped; -2: ran, cluster launch refused
     return {"trial_ms": ms.tolist(), "ctas_per_sm": int(choice[0]), "share_scale": choice[1] / 100.0,
-            "steps": int(np.sum(ms >= 0)) * int(steps_per_trial)}
+            "clusters": bool(choice[2]), "steps": ran * int(steps_per_trial)}
 
 
 def shell_batch_destroy(b: Batch):

@@ -141,6 +141,7 @@ struct shell_batch {
   bool profiling = false;
   int occ = 0;                 // CTAs per SM of the solve launch (0 = the occupancy maximum)
   bool cluster_off = false;    // set if a cluster launch was refused
+  int policy = 0;              // 0 flat teams, 1 one-cluster teams
   double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
   double kern_ms[2] = {0.0, 0.0};
@@ -205,10 +206,12 @@ int rebuild_tables(shell_batch *b) {
   b->prec = (any64 && any32) ? 0 : (any64 ? 1 : 2);
   const int occ_max = blocks_per_sm_cached(b->prec);
   const int occ = (b->occ > 0 && b->occ < occ_max) ? b->occ : occ_max;
-  // thread-block clusters: teams that are whole clusters synchronise with the hardware cluster barrier
-  const int CS = b->cluster_off ? 0 : (max_clusters_cached(b->prec) > 0 ? kCluster : 0);
+  // team policy: flat (multi-CTA teams of any size, cooperative launch, global barriers) or clusters
+  // (multi-CTA teams are exactly one 8-CTA cluster and use the hardware cluster barrier; non-cooperative)
+  const bool use_clusters = b->policy == 1 && !b->cluster_off && max_clusters_cached(b->prec) > 0;
+  const int CS = use_clusters ? kCluster : 0;
   int G = num_sms() * occ;
-  if (CS) G = std::min(G, max_clusters_cached(b->prec) * CS) / CS * CS;
+  if (CS) G = std::max(CS, std::min(G, max_clusters_cached(b->prec) * CS) / CS * CS);
   std::vector<double> work(n);
   double total = 0.0;
   for (int k = 0; k < n; ++k) {
@@ -231,8 +234,7 @@ int rebuild_tables(shell_batch *b) {
     int want = (int)std::floor(work[k] / share);
     if (CS) {
       if (want < CS / 2) break;
-      want = std::max(1, (int)std::lround((double)want / CS)) * CS;
-      want = std::min(want, ((h->h.n_chunks + CS - 1) / CS) * CS);
+      want = CS;
     } else {
       want = std::min(want, h->h.n_chunks);
       if (want < 2) break;
@@ -389,7 +391,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   const int n = b->n_active;
   if (n == 0 || n_steps == 0) {
     if (stats)
-      for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0};
+      for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0, 0.0, 0, 0};
     return SHELL_OK;
   }
   cudaStream_t st = b->mem.st;
@@ -455,7 +457,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
     CK(cudaStreamSynchronize(st));
   }
   if (stats)
-    for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0};
+    for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0, 0.0, 0, 0};
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
     const InstStatus &a = after[k];
@@ -478,6 +480,8 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       o.total_pcg_iterations = a.total_iters - z.total_iters;
       o.rel_residual = a.rel_res;
       o.total_refine_rounds = a.total_rounds - z.total_rounds;
+      o.last_solve_us = a.last_ns * 1e-3;
+      o.team_ctas = a.team_size;
     }
   }
   return first_err;
@@ -1049,6 +1053,8 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
     stats->total_pcg_iterations = after.total_iters - before.total_iters;
     stats->rel_residual = after.rel_res;
     stats->total_refine_rounds = after.total_rounds - before.total_rounds;
+    stats->last_solve_us = after.last_ns * 1e-3;
+    stats->team_ctas = after.team_size;
   }
   if (aborted) return SHELL_ERR_TIMEOUT;
   return after.err;
@@ -1309,12 +1315,14 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
   const double scales[3] = {0.5, 1.0, 2.0};
   double best = 1e300;
   int best_k = 0;
-  for (int k = 0; k < 9; ++k) {
-    const int oi = k / 3, si = k % 3;
-    if (oi == 1 && occs[1] == occs[0]) {
+  for (int k = 0; k < 12; ++k) {
+    const int pol = k < 9 ? 0 : 1;
+    const int oi = k < 9 ? k / 3 : 2, si = k % 3;
+    if ((pol == 0 && oi == 1 && occs[1] == occs[0]) || (pol == 1 && max_clusters_cached(b->prec) == 0)) {
       if (out_ms) out_ms[k] = -1.0;
       continue;
     }
+    b->policy = pol;
     b->occ = occs[oi];
     b->share_scale = scales[si];
     b->dirty = true;
@@ -1323,18 +1331,21 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
     double ms = 0.0;
     for (float t : b->step_ms) ms += t;
     ms /= std::max<size_t>(1, b->step_ms.size());
-    if (out_ms) out_ms[k] = ms;
+    if (pol == 1 && b->cluster_off) ms = 1e300;   // the cluster launch was refused (the steps still ran)
+    if (out_ms) out_ms[k] = ms < 1e299 ? ms : -2.0;
     if (ms < best) {
       best = ms;
       best_k = k;
     }
   }
-  b->occ = occs[best_k / 3];
+  b->policy = best_k < 9 ? 0 : 1;
+  b->occ = occs[best_k < 9 ? best_k / 3 : 2];
   b->share_scale = scales[best_k % 3];
   b->dirty = true;
   if (out_choice) {
     out_choice[0] = b->occ;
     out_choice[1] = (int32_t)std::lround(b->share_scale * 100.0);
+    out_choice[2] = b->policy;
   }
   return SHELL_OK;
 }

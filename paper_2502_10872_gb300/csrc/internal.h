@@ -37,8 +37,9 @@ struct InstStatus {
   long long total_iters;
   double rel_res;       // relative residual of the last committed step
   int32_t fail_step;    // steps_done when the failure happened
-  int32_t pad;
+  int32_t team_size;    // CTAs that solved this instance in the last step
   long long total_rounds;
+  long long last_ns;    // device time of the last step's solve of this instance (right-hand side to commit)
 };
 
 // One level of the smoothed-aggregation multigrid preconditioner (device pointers). Matrices are SELL-32:

@@ -52,6 +52,7 @@ struct Team {
   int mode;     // 0: one CTA; 1: global barrier; 2: one whole cluster; 3: several whole clusters
   int cluster;  // CTAs per cluster
   int *cluster_ok;
+  unsigned long long t0;   // start of the current instance's solve (global timer, ns)
 };
 
 __device__ inline void cluster_barrier() {
@@ -221,9 +222,9 @@ __device__ inline float4 ldg4(const float4 *p) { return *p; }
 // y = A g for one row (SELL-32)
 // g is written by other CTAs during the launch: it must not be read through the non-coherent path, so it
 // carries no __restrict__ / const-restrict qualification. Both forms issue the column, value and gather
-// loads of several nonzeros before consuming them (memory-level parallelism per thread). Matrix columns
-// and values are read once per product and loaded with the streaming hint (evict first), so they do not
-// push the gathered vector, which every row re-reads, out of L1 and L2.
+// loads of several nonzeros before consuming them (memory-level parallelism per thread). Matrix data uses
+// normal caching: the same constant matrix is read by every product of every iteration, so L2 reuse of it
+// matters more than protecting the gathered vector (a streaming hint halved the L2 hit rate).
 //
 // FP64 (refinement residual, FP64 CG): y_i = sum_j a_ij g_j.
 __device__ inline void spmv_row(const Inst &I, const double *__restrict__ val, const D4 *g, int row, double &ax,
@@ -239,8 +240,8 @@ __device__ inline void spmv_row(const Inst &I, const double *__restrict__ val, c
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? __ldcs(I.sl_col + q) : row;
-      a[j] = ok ? __ldcs(val + q) : 0.0;
+      c[j] = ok ? I.sl_col[q] : row;
+      a[j] = ok ? val[q] : 0.0;
     }
     D4 v[U];
 #pragma unroll
@@ -276,8 +277,8 @@ __device__ inline void spmv_row(const Inst &I, const float *__restrict__ val, co
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? __ldcs(I.sl_col + q) : row;
-      a[j] = ok ? __ldcs(val + q) : 0.0f;
+      c[j] = ok ? I.sl_col[q] : row;
+      a[j] = ok ? val[q] : 0.0f;
     }
     float4 v[U];
 #pragma unroll
@@ -479,8 +480,8 @@ __device__ inline void sell_plain(const int32_t *sp, const int32_t *sc, const R 
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? __ldcs(sc + q) : 0;
-      a[j] = ok ? __ldcs(sv + q) : R(0);
+      c[j] = ok ? sc[q] : 0;
+      a[j] = ok ? sv[q] : R(0);
     }
     G t[U];
 #pragma unroll
@@ -511,8 +512,8 @@ __device__ inline void level_a(const AmgDev &L, const float4 *v, int row, float 
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? __ldcs(L.a_col + q) : row;
-      a[j] = ok ? __ldcs(L.a_val32 + q) : 0.0f;
+      c[j] = ok ? L.a_col[q] : row;
+      a[j] = ok ? L.a_val32[q] : 0.0f;
     }
     float4 t[U];
 #pragma unroll
@@ -729,6 +730,8 @@ __device__ void phase_commit(const Inst &I, const Team &tm) {
 __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, int rounds, double rel) {
   if (tm.rank == 0 && threadIdx.x == 0) {
     InstStatus *s = I.status;
+    s->last_ns = (long long)(gtimer() - tm.t0);
+    s->team_size = tm.size;
     if (err == SHELL_OK) {
       s->steps_done += 1;
       s->last_iters = iters;
@@ -855,6 +858,7 @@ __global__ void __launch_bounds__(kBlock, PREC == 2 ? 3 : 2) k_solve(const Inst 
   for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
     const Inst &I = insts[sch.team_list[q]];
     if (I.status->err != SHELL_OK) continue;
+    tm.t0 = gtimer();
     bool ok;
     if (PREC == 1 || (PREC == 0 && I.precision == SHELL_FP64))
       ok = solve_fp64(I, tm);
@@ -879,25 +883,27 @@ int solve_blocks_per_sm(int prec) {
   return n;
 }
 
+// Cluster launches are not cooperative: the scheduler uses clusters only when every team is one CTA or one
+// whole cluster (hardware co-schedules a cluster, and no team waits for CTAs outside its cluster); teams
+// larger than a cluster need the cooperative launch (all CTAs co-resident) and use global barriers.
 cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  int na = 1;
+  cudaLaunchAttribute attr[1];
   if (sched.cluster > 0) {
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = sched.cluster;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    na = 2;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = sched.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
   }
   cfg.attrs = attr;
-  cfg.numAttrs = na;
+  cfg.numAttrs = 1;
   if (prec == 1) return cudaLaunchKernelEx(&cfg, k_solve<1>, d_insts, sched);
   if (prec == 2) return cudaLaunchKernelEx(&cfg, k_solve<2>, d_insts, sched);
   return cudaLaunchKernelEx(&cfg, k_solve<0>, d_insts, sched);

@@ -57,5 +57,5 @@ def test_binding_structs_match_header_layout():
     import ctypes as C
     # shell_options: double, int32(+pad), double, double, int32, int32, 4 pointers
     assert C.sizeof(binding.shell_options) == 8 + 8 + 8 + 8 + 4 + 4 + 4 * 8 + 8
-    assert C.sizeof(binding.shell_step_stats) == 4 * 4 + 8 + 8 + 8
+    assert C.sizeof(binding.shell_step_stats) == 4 * 4 + 8 + 8 + 8 + 8 + 8
     assert C.sizeof(binding.shell_bc) == 8 + 8 + 8 + 24 + 8 + 8 + 8
