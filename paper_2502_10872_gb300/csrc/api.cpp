@@ -108,6 +108,8 @@ struct shell_handle {
   size_t amg_bytes = 0;
   int64_t vcycle_bytes = 0;      // algorithmic bytes of one FP32 V-cycle
   double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
+  long long meas_ns = 0;         // device solve time of the last step (0 = never run)
+  int meas_team = 0;             // team size it ran with
   double sched_est = 64.0;       // estimate the current schedule was planned with
   int64_t nnz = 0, nnz_pad = 0;
   InstStatus last_status{};
@@ -142,6 +144,7 @@ struct shell_batch {
   int occ = 0;                 // CTAs per SM of the solve launch (0 = the occupancy maximum)
   bool cluster_off = false;    // set if a cluster launch was refused
   int policy = 0;              // 0 flat teams, 1 one-cluster teams
+  double plan_T = 0.0;         // makespan the current flat plan was built for (ns, or model units)
   double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
   double kern_ms[2] = {0.0, 0.0};
@@ -212,64 +215,132 @@ int rebuild_tables(shell_batch *b) {
   const int CS = use_clusters ? kCluster : 0;
   int G = num_sms() * occ;
   if (CS) G = std::max(CS, std::min(G, max_clusters_cached(b->prec) * CS) / CS * CS);
+  // single-CTA-equivalent solve time of each instance: measured (last solve time x team size, corrected by
+  // the team-overhead model below) once the instance has run, else rows x iterations
+  constexpr double kBeta = 0.04;   // barrier overhead per extra CTA of a team: t(c) = w/c (1 + beta (c-1))
+  const double beta = kBeta * b->share_scale;
   std::vector<double> work(n);
-  double total = 0.0;
+  bool measured = true;
+  for (int k = 0; k < n; ++k) measured &= b->slots[b->active[k]]->meas_ns > 0;
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
-    work[k] = (double)h->nv * std::max(1.0, h->est_iters) * (h->h.amg_levels > 0 ? 6.0 : 1.0);
+    if (measured) {
+      const double c = std::max(1, h->meas_team);
+      work[k] = (double)h->meas_ns * c / (1.0 + beta * (c - 1.0));
+    } else {
+      work[k] = (double)h->nv * std::max(1.0, h->est_iters) * (h->h.amg_levels > 0 ? 6.0 : 1.0);
+    }
     h->sched_est = h->est_iters;
-    total += work[k];
   }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
-  const double share = total / G / b->share_scale;
   std::vector<int> team_size, team_of(n, -1);
   std::vector<std::vector<int>> team_inst;
   int used = 0;
-  // big instances get their own multi-CTA team sized by their share of the work (whole clusters when the
-  // launch uses clusters; those teams come first, so they start on cluster boundaries)
-  for (int k : order) {
-    const shell_handle *h = b->slots[b->active[k]];
-    int want = (int)std::floor(work[k] / share);
-    if (CS) {
-      if (want < CS / 2) break;
-      want = CS;
+  auto cmax = [&](int k) { return std::max(1, b->slots[b->active[k]]->h.n_chunks); };
+  auto t_of = [&](int k, int c) { return work[k] / c * (1.0 + beta * (c - 1)); };
+  if (CS) {
+    // one-cluster teams for instances that want at least half a cluster, single CTAs for the rest
+    double total = 0.0;
+    for (double w : work) total += w;
+    const double share = total / G;
+    for (int k : order) {
+      if (work[k] / share < CS / 2.0) break;
+      int left_small = 0;
+      for (int q = 0; q < n; ++q)
+        if (team_of[q] < 0 && q != k) ++left_small;
+      if ((G - used - (left_small > 0 ? 1 : 0)) / CS * CS < CS) break;
+      team_of[k] = (int)team_size.size();
+      team_size.push_back(CS);
+      team_inst.push_back({k});
+      used += CS;
+    }
+  } else {
+    // makespan T: instances slower than T on one CTA get the smallest team that meets T; the others are
+    // packed first-fit-decreasing onto single CTAs of capacity T; bisect for the smallest T that fits G
+    auto team_for = [&](int k, double T) {
+      int c = 1;
+      while (c < cmax(k) && t_of(k, c) > T) ++c;
+      return c;
+    };
+    auto plan = [&](double T, std::vector<int> *sizes, std::vector<std::vector<int>> *bins) -> int {
+      int need = 0;
+      std::vector<double> load;
+      std::vector<std::vector<int>> bl;
+      for (int k : order) {
+        if (t_of(k, 1) > T) {
+          const int c = team_for(k, T);
+          need += c;
+          if (sizes) sizes->push_back(c);
+        } else {
+          size_t q = 0;
+          while (q < load.size() && load[q] + t_of(k, 1) > T) ++q;
+          if (q == load.size()) {
+            load.push_back(0.0);
+            bl.emplace_back();
+          }
+          load[q] += t_of(k, 1);
+          bl[q].push_back(k);
+        }
+      }
+      if (bins) *bins = bl;
+      return need + (int)load.size();
+    };
+    double lo = 0.0, hi = 0.0;
+    for (int k = 0; k < n; ++k) {
+      lo = std::max(lo, t_of(k, cmax(k)));
+      hi += work[k];
+    }
+    if (plan(lo, nullptr, nullptr) > G) {
+      for (int it = 0; it < 60 && hi > lo * (1.0 + 1e-3); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        (plan(mid, nullptr, nullptr) <= G ? hi : lo) = mid;
+      }
     } else {
-      want = std::min(want, h->h.n_chunks);
-      if (want < 2) break;
+      hi = lo;
     }
-    int left_small = 0;
-    for (int q = 0; q < n; ++q)
-      if (team_of[q] < 0 && q != k) ++left_small;
-    int room = G - used - (left_small > 0 ? 1 : 0);
-    if (CS) room = room / CS * CS;
-    want = std::min(want, room);
-    if (want < (CS ? CS : 2)) break;
-    team_of[k] = (int)team_size.size();
-    team_size.push_back(want);
-    team_inst.push_back({k});
-    used += want;
-  }
-  // the rest: single-CTA teams, longest-processing-time first
-  std::vector<int> small;
-  for (int k : order)
-    if (team_of[k] < 0) small.push_back(k);
-  if (!small.empty()) {
-    const int n1 = std::max(1, std::min((int)small.size(), G - used));
-    const int first = (int)team_size.size();
-    std::vector<double> load(n1, 0.0);
-    for (int q = 0; q < n1; ++q) {
+    std::vector<int> sizes;
+    std::vector<std::vector<int>> bins;
+    plan(hi, &sizes, &bins);
+    b->plan_T = measured ? hi : 0.0;
+    int q = 0;
+    for (int k : order) {
+      if (t_of(k, 1) > hi) {
+        team_of[k] = (int)team_size.size();
+        team_size.push_back(sizes[q++]);
+        team_inst.push_back({k});
+        used += team_size.back();
+      }
+    }
+    for (auto &bl : bins) {
+      for (int k : bl) team_of[k] = (int)team_size.size();
       team_size.push_back(1);
-      team_inst.push_back({});
+      team_inst.push_back(bl);
+      used += 1;
     }
-    for (int k : small) {
-      int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-      load[best] += work[k];
-      team_inst[first + best].push_back(k);
-      team_of[k] = first + best;
+  }
+  if (CS) {
+    // the rest: single-CTA teams, longest-processing-time first
+    std::vector<int> small;
+    for (int k : order)
+      if (team_of[k] < 0) small.push_back(k);
+    if (!small.empty()) {
+      const int n1 = std::max(1, std::min((int)small.size(), G - used));
+      const int first = (int)team_size.size();
+      std::vector<double> load(n1, 0.0);
+      for (int q = 0; q < n1; ++q) {
+        team_size.push_back(1);
+        team_inst.push_back({});
+      }
+      for (int k : small) {
+        int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[best] += work[k];
+        team_inst[first + best].push_back(k);
+        team_of[k] = first + best;
+      }
+      used += n1;
     }
-    used += n1;
   }
   const int n_teams = (int)team_size.size();
   const int grid = CS ? (used + CS - 1) / CS * CS : used;   // whole clusters; spare CTAs return at once
@@ -468,7 +539,13 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
     if (done > 0) {
       const double it = double(a.total_iters - z.total_iters + 2 * (a.total_rounds - z.total_rounds)) / done;
       h->est_iters = std::max(1.0, it);
-      // results do not depend on the schedule, so re-plan freely when the work estimate moved
+      // results do not depend on the schedule, so re-plan freely when the work estimate moved: on the first
+      // measurement, and when the measured solve time leaves the planned makespan by more than 25 %
+      const bool first_meas = h->meas_ns == 0;
+      h->meas_ns = a.last_ns;
+      h->meas_team = a.team_size;
+      if (first_meas) b->dirty = true;
+      if (b->policy == 0 && b->plan_T > 0 && h->meas_ns > 1.25 * b->plan_T) b->dirty = true;
       if (std::fabs(h->est_iters - h->sched_est) > 0.25 * h->sched_est) b->dirty = true;
     }
     if (stats) {

@@ -538,34 +538,40 @@ __device__ inline void level_a(const AmgDev &L, const D4 *v, int row, double &ax
   }                    \
   }
 
+// Pre-smoothing of level 0 from zero, row-local: b0 = r, x0 = omega D0^-1 r. It runs right after the phase
+// that wrote r for these rows (same thread), so it needs no barrier of its own.
+template <typename R>
+__device__ void vcycle_pre0(const Inst &I, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const AmgDev &A = I.amg[0];
+  const R *rin = reinterpret_cast<const R *>(I.r);
+  const int nv = I.nv;
+  G *b = reinterpret_cast<G *>(A.b);
+  G *x = reinterpret_cast<G *>(A.x);
+  const R *dinv = LevelVal<R>::dinv(A);
+  const R om = R(A.omega);
+  LEVEL_ROWS_BEGIN(A.n, tm)
+  const R r0 = rin[row], r1 = rin[nv + row], r2 = rin[2 * nv + row];
+  b[row] = Vec<R>::mk(r0, r1, r2);
+  const R d = om * dinv[row];
+  x[row] = Vec<R>::mk(d * r0, d * r1, d * r2);
+  LEVEL_ROWS_END
+}
+
 // u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing, Galerkin coarse operators and a dense
-// coarsest solve; input the CG residual r (SoA), output u in g (AoS). Returns false on abort.
+// coarsest solve; output u in g (AoS). Expects vcycle_pre0 and a team barrier before it. The pre-smoothing
+// of each coarser level is fused into the restriction that produces its right-hand side. Returns false on
+// abort.
 template <typename R>
 __device__ bool vcycle(const Inst &I, const Team &tm) {
   typedef typename Vec<R>::G G;
   const int L = I.amg_levels;
-  const R *rin = reinterpret_cast<const R *>(I.r);
-  const int nv = I.nv;
   // ---- down
   for (int l = 0; l < L - 1; ++l) {
     const AmgDev &A = I.amg[l];
     G *b = reinterpret_cast<G *>(A.b);
     G *x = reinterpret_cast<G *>(A.x);
     G *rr = reinterpret_cast<G *>(A.r);
-    const R *dinv = LevelVal<R>::dinv(A);
-    const R om = R(A.omega);
-    LEVEL_ROWS_BEGIN(A.n, tm)
-    G bi;
-    if (l == 0) {
-      bi = Vec<R>::mk(rin[row], rin[nv + row], rin[2 * nv + row]);
-      b[row] = bi;
-    } else {
-      bi = ldg4(b + row);
-    }
-    const R d = om * dinv[row];
-    x[row] = Vec<R>::mk(d * R(bi.x), d * R(bi.y), d * R(bi.z));
-    LEVEL_ROWS_END
-    if (!team_sync(tm)) return false;
     LEVEL_ROWS_BEGIN(A.n, tm)
     R ax, ay, az;
     level_a(A, x, row, ax, ay, az);
@@ -573,11 +579,20 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
     rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
     LEVEL_ROWS_END
     if (!team_sync(tm)) return false;
-    G *bc = reinterpret_cast<G *>(I.amg[l + 1].b);
+    const AmgDev &C = I.amg[l + 1];
+    G *bc = reinterpret_cast<G *>(C.b);
+    G *xc = reinterpret_cast<G *>(C.x);
+    const R *dinvc = LevelVal<R>::dinv(C);
+    const R omc = R(C.omega);
+    const bool pre = l + 1 < L - 1;   // the coarsest level is solved, not smoothed
     LEVEL_ROWS_BEGIN(A.n_next, tm)
     R ax, ay, az;
     sell_plain<R, G>(A.r_ptr, A.r_col, LevelVal<R>::r(A), rr, row, ax, ay, az);
     bc[row] = Vec<R>::mk(ax, ay, az);
+    if (pre) {
+      const R d = omc * dinvc[row];
+      xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
+    }
     LEVEL_ROWS_END
     if (!team_sync(tm)) return false;
   }
@@ -666,6 +681,7 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
 // -3 on a non-finite reduction.
 template <typename R>
 __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, double *rho_out) {
+  if (I.amg_levels > 0) vcycle_pre0<R>(I, tm);
   if (!team_sync(tm)) return -2;
   if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
   phase_spmv<R>(I, tm);
@@ -680,6 +696,7 @@ __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, d
   bool first = true;
   for (int it = 1; it <= max_it; ++it) {
     phase_update<R>(I, tm, R(alpha), R(beta), first, x);
+    if (I.amg_levels > 0) vcycle_pre0<R>(I, tm);
     if (!team_sync(tm)) return -2;
     if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
     phase_spmv<R>(I, tm);
