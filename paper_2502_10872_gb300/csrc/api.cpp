@@ -144,6 +144,7 @@ struct shell_batch {
   int occ = 0;                 // CTAs per SM of the solve launch (0 = the occupancy maximum)
   bool cluster_off = false;    // set if a cluster launch was refused
   int policy = 0;              // 0 flat teams, 1 one-cluster teams
+  int occ_launch = 3;          // occupancy variant of the current plan
   double plan_T = 0.0;         // makespan the current flat plan was built for (ns, or model units)
   double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
@@ -152,11 +153,14 @@ struct shell_batch {
 
 namespace {
 
-int blocks_per_sm_cached(int prec) {
-  static int n[3] = {-1, -1, -1};
-  if (n[prec] < 0) n[prec] = std::max(1, solve_blocks_per_sm(prec));
-  return n[prec];
+// CTAs per SM of the solve variant compiled for `occ` (FP32: variants for 3, 4, 5; others one variant)
+int blocks_per_sm_cached(int prec, int occ = 3) {
+  static int n[3][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  occ = std::max(1, std::min(5, occ));
+  if (n[prec][occ] < 0) n[prec][occ] = std::max(1, solve_blocks_per_sm(prec, occ));
+  return n[prec][occ];
 }
+int max_occ(int prec) { return prec == 2 ? blocks_per_sm_cached(2, 5) : blocks_per_sm_cached(prec, 2); }
 int max_clusters_cached(int prec) {
   static int n[3] = {-1, -1, -1};
   if (n[prec] < 0) n[prec] = std::max(0, solve_max_clusters(prec, kCluster));
@@ -207,8 +211,10 @@ int rebuild_tables(shell_batch *b) {
   bool any64 = false, any32 = false;
   for (int k = 0; k < n; ++k) (b->slots[b->active[k]]->h.precision == SHELL_FP64 ? any64 : any32) = true;
   b->prec = (any64 && any32) ? 0 : (any64 ? 1 : 2);
-  const int occ_max = blocks_per_sm_cached(b->prec);
-  const int occ = (b->occ > 0 && b->occ < occ_max) ? b->occ : occ_max;
+  // default occupancy: the 3-CTA variant for FP32 (fewest spills), else the variant's maximum
+  const int occ_def = b->prec == 2 ? blocks_per_sm_cached(2, 3) : max_occ(b->prec);
+  const int occ = (b->occ > 0) ? std::min(b->occ, max_occ(b->prec)) : occ_def;
+  b->occ_launch = occ;
   // team policy: flat (multi-CTA teams of any size, cooperative launch, global barriers) or clusters
   // (multi-CTA teams are exactly one 8-CTA cluster and use the hardware cluster barrier; non-cooperative)
   const bool use_clusters = b->policy == 1 && !b->cluster_off && max_clusters_cached(b->prec) > 0;
@@ -411,12 +417,12 @@ int rebuild_tables(shell_batch *b) {
 // the solve launch; if the driver refuses the cluster launch, fall back to plain global team barriers (the
 // team layout stays valid: whole-cluster teams become flat global-barrier teams)
 cudaError_t solve_launch(shell_batch *b, cudaStream_t st) {
-  cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, st);
+  cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, b->occ_launch, st);
   if (e != cudaSuccess && b->sched.cluster > 0) {
     cudaGetLastError();
     b->cluster_off = true;
     b->sched.cluster = 0;
-    e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, st);
+    e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, b->occ_launch, st);
   }
   return e;
 }
@@ -1110,7 +1116,7 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
   if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
   const int prec = h->h.precision == SHELL_FP64 ? 1 : 2;
-  int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(prec), h->h.n_chunks));
+  int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(prec, prec == 2 ? 3 : 2), h->h.n_chunks));
   if (team > static_max_ctas()) return SHELL_ERR_STATIC_LIMIT;
   const InstStatus before = h->last_status;
   InstStatus after{};
@@ -1387,15 +1393,20 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
     if (rc != SHELL_OK) return rc;
   }
   if (b->n_active == 0) return SHELL_OK;
-  const int occ_max = blocks_per_sm_cached(b->prec);
-  const int occs[3] = {1, std::max(1, occ_max / 2), occ_max};
+  const int occ_max = max_occ(b->prec);
+  int occs[3] = {1, std::max(1, occ_max / 2), occ_max};
+  if (b->prec == 2) {   // the FP32 variants compiled for 3, 4 and 5 CTAs per SM
+    occs[0] = blocks_per_sm_cached(2, 3);
+    occs[1] = blocks_per_sm_cached(2, 4);
+    occs[2] = blocks_per_sm_cached(2, 5);
+  }
   const double scales[3] = {0.5, 1.0, 2.0};
   double best = 1e300;
   int best_k = 0;
   for (int k = 0; k < 12; ++k) {
     const int pol = k < 9 ? 0 : 1;
     const int oi = k < 9 ? k / 3 : 2, si = k % 3;
-    if ((pol == 0 && oi == 1 && occs[1] == occs[0]) || (pol == 1 && max_clusters_cached(b->prec) == 0)) {
+    if ((pol == 0 && oi > 0 && occs[oi] == occs[oi - 1]) || (pol == 1 && max_clusters_cached(b->prec) == 0)) {
       if (out_ms) out_ms[k] = -1.0;
       continue;
     }

@@ -176,7 +176,7 @@ cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles,
                           cudaStream_t st);
 cudaError_t launch_gather_forces(const Inst *d_inst, const Inst &h_inst, double *d_out, cudaStream_t st);
 cudaError_t launch_energy_reduce(const Inst *d_inst, const Inst &h_inst, double *d_out4, cudaStream_t st);
-cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, cudaStream_t st);
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, int occ, cudaStream_t st);
 cudaError_t launch_aos_to_soa(const double *src, double *dst, int nv, cudaStream_t st);
 cudaError_t launch_soa_to_aos(const double *src, double *dst, int nv, cudaStream_t st);
 cudaError_t launch_mass(const Inst *d_inst, const Inst &h_inst, double rho, const double g[3], int n_loads,
@@ -185,7 +185,7 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
                                  int32_t *d_out_abort, cudaStream_t st);
 cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
                            cudaStream_t st);
-int solve_blocks_per_sm(int prec);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
+int solve_blocks_per_sm(int prec, int occ);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
 int solve_max_clusters(int prec, int cluster);   // co-resident clusters of the solve kernel, 0 if unsupported
 constexpr int kCluster = 8;                      // cluster size of the batched solve launch (portable)
 int static_max_ctas();

@@ -852,10 +852,11 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
   return true;
 }
 
-// PREC: 0 = instances of either precision, 1 = FP64 instances only, 2 = FP32-refinement instances only (the
-// single-precision variants need fewer registers, so more CTAs fit on an SM).
-template <int PREC>
-__global__ void __launch_bounds__(kBlock, PREC == 2 ? 3 : 2) k_solve(const Inst *__restrict__ insts, Sched sch) {
+// PREC: 0 = instances of either precision, 1 = FP64 instances only, 2 = FP32-refinement instances only.
+// MINB: CTAs per SM the register allocation is bounded for (the FP32 variant is compiled for 3, 4 and 5;
+// more resident warps mean more loads in flight, at the price of register spills; the autotuner picks).
+template <int PREC, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__ insts, Sched sch) {
   Team tm;
   tm.team = sch.cta_team[blockIdx.x];
   if (tm.team < 0) return;
@@ -889,21 +890,28 @@ __global__ void __launch_bounds__(kBlock, PREC == 2 ? 3 : 2) k_solve(const Inst 
 
 }  // namespace
 
-int solve_blocks_per_sm(int prec) {
+// kernel of a precision mode and an occupancy variant (FP32: 3, 4 or 5 CTAs per SM; others: 2)
+typedef void (*SolveFn)(const Inst *, Sched);
+static SolveFn solve_fn(int prec, int occ) {
+  if (prec == 2) {
+    if (occ >= 5) return k_solve<2, 5>;
+    if (occ == 4) return k_solve<2, 4>;
+    return k_solve<2, 3>;
+  }
+  if (prec == 1) return k_solve<1, 2>;
+  return k_solve<0, 2>;
+}
+
+int solve_blocks_per_sm(int prec, int occ) {
   int n = 0;
-  if (prec == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<1>, kBlock, 0);
-  else if (prec == 2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<2>, kBlock, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_solve<0>, kBlock, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_fn(prec, occ), kBlock, 0);
   return n;
 }
 
 // Cluster launches are not cooperative: the scheduler uses clusters only when every team is one CTA or one
 // whole cluster (hardware co-schedules a cluster, and no team waits for CTAs outside its cluster); teams
 // larger than a cluster need the cooperative launch (all CTAs co-resident) and use global barriers.
-cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, cudaStream_t st) {
+cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, int occ, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
@@ -921,9 +929,7 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int 
   }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (prec == 1) return cudaLaunchKernelEx(&cfg, k_solve<1>, d_insts, sched);
-  if (prec == 2) return cudaLaunchKernelEx(&cfg, k_solve<2>, d_insts, sched);
-  return cudaLaunchKernelEx(&cfg, k_solve<0>, d_insts, sched);
+  return cudaLaunchKernelEx(&cfg, solve_fn(prec, occ), d_insts, sched);
 }
 
 int solve_max_clusters(int prec, int cluster) {
@@ -938,13 +944,7 @@ int solve_max_clusters(int prec, int cluster) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  cudaError_t e;
-  if (prec == 1)
-    e = cudaOccupancyMaxActiveClusters(&n, k_solve<1>, &cfg);
-  else if (prec == 2)
-    e = cudaOccupancyMaxActiveClusters(&n, k_solve<2>, &cfg);
-  else
-    e = cudaOccupancyMaxActiveClusters(&n, k_solve<0>, &cfg);
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, solve_fn(prec, 3), &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -1027,7 +1027,7 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (kBarWords + 2), st)) != cudaSuccess) return e;
   for (int k = 0; k < n_steps; ++k) {
     if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st)) != cudaSuccess) return e;
-    if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, st)) != cudaSuccess) return e;
+    if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, 3, st)) != cudaSuccess) return e;
   }
   if ((e = launch_gather_status(d_inst, 1, status_out, sc.abort_flag, abort_out, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(h_status, status_out, sizeof(InstStatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
