@@ -88,13 +88,28 @@ def measured_traffic(workload_name):
     return float(kv["traffic_bytes_per_launch"])
 
 
+def rank_seed(seed, rank):
+    """Seed of a rank's own batch: weak scaling gives every rank an independent batch of the same size."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(value, world, device=None):
+    """Slowest rank's time (MAX all-reduce); the only collective of the benchmark, outside the data path."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(name, seed, rank):
     import shellgen as sg
     if name == "batch256":
-        return sg.mixed_batch(256, seed=seed + 1000 * rank, steps=500), "256 mixed instances, side 8-128 cells"
+        return sg.mixed_batch(256, seed=rank_seed(seed, rank), steps=500), "256 mixed instances, side 8-128 cells"
     if name.startswith("batch"):
         n = int(name[5:])
-        return sg.mixed_batch(n, seed=seed + 1000 * rank, steps=500), f"{n} mixed instances"
+        return sg.mixed_batch(n, seed=rank_seed(seed, rank), steps=500), f"{n} mixed instances"
     if name == "cyl128":
         return [sg.cylinder_panel(128, "SS")], "cylinder panel 128x128 cells, SS"
     if name == "jitter512":
@@ -199,7 +214,7 @@ def serve(args, gb, torch, dev, rank, world):
     import shellgen as sg
     from paper_2502_10872_gb300.serving import Request, Server
     torch.cuda.set_stream(torch.cuda.Stream())
-    arrivals = sg.serving_requests(args.serve_requests, rate_hz=200.0, seed=args.seed + 1000 * rank)
+    arrivals = sg.serving_requests(args.serve_requests, rate_hz=200.0, seed=rank_seed(args.seed, rank))
     reqs = [Request(k, t, sc, sc.steps) for k, (t, sc) in enumerate(arrivals)]
     srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), precision="fp32_refine")
     with Clocks(dev) as clk:
@@ -304,11 +319,7 @@ def main():
     with Clocks(dev) as clk:
         stats32, times32, kern32, wall32 = timed(b32, K, W, profile=True, tune_key="fp32_refine")
     dev_s = float(np.sum(times32)) / 1000.0
-    t_rank = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t_rank, op=dist.ReduceOp.MAX)
-    t_max = float(t_rank.item())
+    t_max = max_over_ranks(dev_s, world, device="cuda")
     value = V_total * K * world / t_max
     p50, p99 = float(np.percentile(times32, 50)), float(np.percentile(times32, 99))
 

@@ -135,32 +135,55 @@ __device__ inline float warp_sum(float v) {
   return v;
 }
 
-// reduce three per-thread values of one chunk (fixed tree) and store them as the chunk's partial
-template <typename A>
-__device__ void chunk_reduce(A v0, A v1, A v2, double *dst) {
-  __shared__ double sm[kBlock / 32][3];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v0 = warp_sum(v0);
-  v1 = warp_sum(v1);
-  v2 = warp_sum(v2);
-  if (lane == 0) {
-    sm[warp][0] = double(v0);
-    sm[warp][1] = double(v1);
-    sm[warp][2] = double(v2);
-  }
+// Per-chunk partials: each chunk's three values are reduced by a fixed tree (warp shuffles, then the warps
+// in order). The warp sums of up to kStage chunks are staged in shared memory and written out together, so
+// a CTA that owns several chunks of a phase pays two __syncthreads per kStage chunks instead of per chunk.
+constexpr int kStage = 32;
+
+struct ChunkStage {
+  int n = 0;       // staged chunks
+  int first = 0;   // chunk id of the first staged one
+};
+
+__device__ inline double (*stage_buf())[kBlock / 32][3] {
+  __shared__ double sm[kStage][kBlock / 32][3];
+  return sm;
+}
+
+__device__ void stage_flush(ChunkStage &cs, const Inst &I, const Team &tm) {
+  double(*sm)[kBlock / 32][3] = stage_buf();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a0 = sm[0][0], a1 = sm[0][1], a2 = sm[0][2];
+  if ((int)threadIdx.x < cs.n) {
+    const int k = threadIdx.x;
+    double a0 = sm[k][0][0], a1 = sm[k][0][1], a2 = sm[k][0][2];
     for (int w = 1; w < kBlock / 32; ++w) {
-      a0 += sm[w][0];
-      a1 += sm[w][1];
-      a2 += sm[w][2];
+      a0 += sm[k][w][0];
+      a1 += sm[k][w][1];
+      a2 += sm[k][w][2];
     }
+    double *dst = part_of(I, tm, cs.first + k * tm.size);
     dst[0] = a0;
     dst[1] = a1;
     dst[2] = a2;
   }
   __syncthreads();
+  cs.n = 0;
+}
+
+template <typename A>
+__device__ void stage_chunk(ChunkStage &cs, const Inst &I, const Team &tm, int ch, A v0, A v1, A v2) {
+  double(*sm)[kBlock / 32][3] = stage_buf();
+  if (cs.n == 0) cs.first = ch;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v0 = warp_sum(v0);
+  v1 = warp_sum(v1);
+  v2 = warp_sum(v2);
+  if (lane == 0) {
+    sm[cs.n][warp][0] = double(v0);
+    sm[cs.n][warp][1] = double(v1);
+    sm[cs.n][warp][2] = double(v2);
+  }
+  if (++cs.n == kStage) stage_flush(cs, I, tm);
 }
 
 // sum all chunk partials of an instance in a fixed order; result broadcast to the CTA. Flips the bank, so
@@ -308,6 +331,7 @@ template <typename RC>
 __device__ void phase_rhs(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   const RC *con = reinterpret_cast<const RC *>(I.contrib);
+  ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
     double bb = 0.0;
     for (int rr = 0; rr < I.rows_per_thread; ++rr) {
@@ -334,8 +358,9 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
       }
       reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
     }
-    chunk_reduce<double>(bb, 0.0, 0.0, part_of(I, tm, ch));
+    stage_chunk<double>(cs, I, tm, ch, bb, 0.0, 0.0);
   }
+  if (cs.n) stage_flush(cs, I, tm);
 }
 
 // FP64 residual r64 = b - A64 sol; returns partial ||r64||^2. If R is float also prepares the inner CG:
@@ -348,6 +373,7 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
   R *xs = reinterpret_cast<R *>(I.xs);
   typename Vec<R>::G *g = Vec<R>::g(I);
   const R *dinv = Vec<R>::dinv(I);
+  ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
     double rr2 = 0.0;
     for (int rr = 0; rr < I.rows_per_thread; ++rr) {
@@ -372,8 +398,9 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
       const R di = dinv[row];
       g[row] = Vec<R>::mk(di * q0, di * q1, di * q2);
     }
-    chunk_reduce<double>(rr2, 0.0, 0.0, part_of(I, tm, ch));
+    stage_chunk<double>(cs, I, tm, ch, rr2, 0.0, 0.0);
   }
+  if (cs.n) stage_flush(cs, I, tm);
 }
 
 // w = A u (u = g); partials (r,u), (w,u), (r,r)
@@ -384,6 +411,7 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
   const typename Vec<R>::G *g = Vec<R>::g(I);
   const R *r = reinterpret_cast<const R *>(I.r);
   R *w = reinterpret_cast<R *>(I.w);
+  ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
     R gu = R(0), wu = R(0), rr2 = R(0);
     for (int rr = 0; rr < I.rows_per_thread; ++rr) {
@@ -400,8 +428,9 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
       wu += ax * R(u.x) + ay * R(u.y) + az * R(u.z);
       rr2 += r0 * r0 + r1 * r1 + r2 * r2;
     }
-    chunk_reduce<R>(gu, wu, rr2, part_of(I, tm, ch));
+    stage_chunk<R>(cs, I, tm, ch, gu, wu, rr2);
   }
+  if (cs.n) stage_flush(cs, I, tm);
 }
 
 // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; then (Jacobi) u = D^-1 r -> g. With the

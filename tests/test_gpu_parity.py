@@ -126,7 +126,7 @@ def test_cylinder128_fp32_refine(model):
     """FP32 forces and PCG with FP64 refinement on the 128 x 128 cylinder: solve to refine_rtol = 1e-10;
     the remaining difference to the FP64 oracle is the FP32 rounding of the force (stated bound 1e-6)."""
     sc = sg.cylinder_panel(128, model)
-    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 10, precision="fp32_refine")
+    m, h, st, (xg, vg), (xo, vo) = run_both(sc, 10, precision="fp32_refine", refine_rtol=1e-10)
     assert st["refine_rounds"] >= 1
     assert st["rel_residual"] <= 1e-10
     assert rel(xg, xo, xo - sc.x0) <= 1e-6, model
