@@ -238,6 +238,13 @@ int shell_batch_retire(shell_batch *b, int32_t slot);
  * first error met, or SHELL_OK. */
 int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats);
 int shell_batch_capacity(shell_batch *b);
+/* Packed state transfer for every resident instance in one copy each way: x and v are host buffers of
+ * [rows][3] FP64 (pinned memory recommended), the instances' rows concatenated in increasing slot order.
+ * shell_batch_state_layout returns the number of resident instances and fills (either may be NULL)
+ * slots[k] (the k-th resident slot) and row_offsets[k] (its first row; row_offsets[count] = rows). */
+int shell_batch_get_states(shell_batch *b, double *x, double *v);
+int shell_batch_set_states(shell_batch *b, const double *x, const double *v);
+int shell_batch_state_layout(shell_batch *b, int32_t *slots, int64_t *row_offsets);
 /* Device time of the last shell_batch_step, per step, in milliseconds: out[k] for k < n (n <= steps). */
 int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
 /* Kernel timing of later shell_batch_step calls: with on != 0 every step is launched directly (not from

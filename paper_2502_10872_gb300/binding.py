@@ -39,7 +39,7 @@ EXPORTS = (
     "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
-    "shell_batch_autotune",
+    "shell_batch_autotune", "shell_batch_get_states", "shell_batch_set_states", "shell_batch_state_layout",
     "shell_batch_destroy",
 )
 
@@ -131,6 +131,9 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_set_profiling": (C.c_int, [P, C.c_int32]),
         "shell_batch_kernel_times": (C.c_int, [P, P]),
         "shell_batch_autotune": (C.c_int, [P, C.c_int32, P, P]),
+        "shell_batch_get_states": (C.c_int, [P, P, P]),
+        "shell_batch_set_states": (C.c_int, [P, P, P]),
+        "shell_batch_state_layout": (C.c_int, [P, P, P]),
         "shell_batch_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
@@ -459,6 +462,35 @@ def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:
     ran = int(np.sum(ms != -1.0))     # -1: skipped; -2: ran, cluster launch refused
     return {"trial_ms": ms.tolist(), "ctas_per_sm": int(choice[0]), "share_scale": choice[1] / 100.0,
             "clusters": bool(choice[2]), "steps": ran * int(steps_per_trial)}
+
+
+def shell_batch_state_layout(b: Batch):
+    """(slots, row_offsets) of the packed state layout: resident slots in increasing order."""
+    lib = load_library()
+    n = lib.shell_batch_state_layout(b.ptr, None, None)
+    slots = np.zeros(max(1, n), np.int32)
+    offs = np.zeros(n + 1, np.int64)
+    lib.shell_batch_state_layout(b.ptr, slots.ctypes.data, offs.ctypes.data)
+    return slots[:n], offs
+
+
+def shell_batch_get_states(b: Batch, x_out=None, v_out=None):
+    """Packed [rows][3] FP64 positions and velocities of every resident instance (one copy each way)."""
+    _, offs = shell_batch_state_layout(b)
+    rows = int(offs[-1])
+    x = np.empty((rows, 3), np.float64) if x_out is None else x_out
+    v = np.empty((rows, 3), np.float64) if v_out is None else v_out
+    assert x.flags.c_contiguous and v.flags.c_contiguous and x.shape == (rows, 3) and v.shape == (rows, 3)
+    _check(load_library().shell_batch_get_states(b.ptr, x.ctypes.data, v.ctypes.data), "shell_batch_get_states")
+    return x, v
+
+
+def shell_batch_set_states(b: Batch, x, v):
+    _, offs = shell_batch_state_layout(b)
+    rows = int(offs[-1])
+    xa = _arr(x, np.float64, (rows, 3))
+    va = _arr(v, np.float64, (rows, 3))
+    _check(load_library().shell_batch_set_states(b.ptr, xa.ctypes.data, va.ctypes.data), "shell_batch_set_states")
 
 
 def shell_batch_destroy(b: Batch):

@@ -135,6 +135,10 @@ struct shell_batch {
   int n_active = 0;
   InstStatus *d_status_out = nullptr;
   int32_t *d_abort_out = nullptr;
+  long long *d_offs = nullptr;     // first row of each active instance in the packed state layout
+  long long rows_total = 0;
+  double *d_pack = nullptr;        // packed states [rows][3] x, then [rows][3] v (allocated on first use)
+  size_t pack_bytes = 0;
   std::vector<int> active;   // slot ids in table order
   std::vector<cudaEvent_t> events;
   std::vector<float> step_ms;
@@ -380,6 +384,7 @@ int rebuild_tables(shell_batch *b) {
     b->sched.cluster_ok = C.take<int32_t>(grid / (CS ? CS : 1) + 1);
     b->d_status_out = C.take<InstStatus>(n);
     b->d_abort_out = C.take<int32_t>(1);
+    b->d_offs = C.take<long long>(n + 1);
   };
   layout(cv);
   if (cv.off > b->tbl_bytes) {
@@ -405,6 +410,10 @@ int rebuild_tables(shell_batch *b) {
   CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_ptr, tptr.data(), 4 * (n_teams + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_list, tlist.data(), 4 * tlist.size(), cudaMemcpyHostToDevice, st));
+  std::vector<long long> offs(n + 1, 0);
+  for (int k = 0; k < n; ++k) offs[k + 1] = offs[k] + b->slots[b->active[k]]->nv;
+  b->rows_total = offs[n];
+  CK(cudaMemcpyAsync(b->d_offs, offs.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(b->sched.bar, 0, sizeof(unsigned int) * kBarWords * n_teams, st));
   CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
@@ -586,6 +595,7 @@ int batch_new(const shell_options *opt, size_t budget, bool solo, shell_batch **
 
 void batch_free(shell_batch *b) {
   if (!b) return;
+  if (b->d_pack) b->mem.put(b->d_pack, b->pack_bytes);
   destroy_graph(b);
   for (cudaEvent_t e : b->events) cudaEventDestroy(e);
   for (cudaEvent_t e : b->pev) cudaEventDestroy(e);
@@ -1376,6 +1386,62 @@ int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats) {
 }
 
 int shell_batch_capacity(shell_batch *b) { return b ? (int)b->slots.size() : 0; }
+
+// packed state transfer of every resident instance (rows in increasing slot order)
+static int batch_states(shell_batch *b, double *x, double *v, const double *xin, const double *vin) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  if (b->dirty) {
+    int rc = rebuild_tables(b);
+    if (rc != SHELL_OK) return rc;
+  }
+  if (b->n_active == 0) return SHELL_OK;
+  const size_t need = 48 * (size_t)b->rows_total;
+  if (b->pack_bytes < need) {
+    if (b->d_pack) b->mem.put(b->d_pack, b->pack_bytes);
+    b->d_pack = (double *)b->mem.get(need);
+    b->pack_bytes = b->d_pack ? need : 0;
+    if (!b->d_pack) return SHELL_ERR_OOM;
+  }
+  cudaStream_t st = b->mem.st;
+  const size_t n3 = 3 * (size_t)b->rows_total;
+  double *dx = b->d_pack, *dv = b->d_pack + n3;
+  if (xin) {
+    CK(cudaMemcpyAsync(dx, xin, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dv, vin, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 1, st));
+  } else {
+    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 0, st));
+    CK(cudaMemcpyAsync(x, dx, 8 * n3, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(v, dv, 8 * n3, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  return SHELL_OK;
+}
+
+int shell_batch_get_states(shell_batch *b, double *x, double *v) {
+  if (!x || !v) return SHELL_ERR_INVALID_ARG;
+  return batch_states(b, x, v, nullptr, nullptr);
+}
+
+int shell_batch_set_states(shell_batch *b, const double *x, const double *v) {
+  if (!x || !v) return SHELL_ERR_INVALID_ARG;
+  return batch_states(b, nullptr, nullptr, x, v);
+}
+
+int shell_batch_state_layout(shell_batch *b, int32_t *slots, int64_t *row_offsets) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  int k = 0;
+  int64_t off = 0;
+  for (size_t q = 0; q < b->slots.size(); ++q)
+    if (b->slots[q]) {
+      if (slots) slots[k] = (int32_t)q;
+      if (row_offsets) row_offsets[k] = off;
+      off += b->slots[q]->nv;
+      ++k;
+    }
+  if (row_offsets) row_offsets[k] = off;
+  return k;
+}
 
 int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n) {
   if (!b || !out_ms || n < 0) return SHELL_ERR_INVALID_ARG;

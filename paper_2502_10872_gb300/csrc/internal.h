@@ -185,6 +185,8 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
                                  int32_t *d_out_abort, cudaStream_t st);
 cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double *d_in, double *d_out,
                            cudaStream_t st);
+cudaError_t launch_pack_states(const Inst *d_insts, int n, const long long *d_offs, long long rows, double *d_x,
+                               double *d_v, int unpack, cudaStream_t st);
 int solve_blocks_per_sm(int prec, int occ);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
 int solve_max_clusters(int prec, int cluster);   // co-resident clusters of the solve kernel, 0 if unsupported
 constexpr int kCluster = 8;                      // cluster size of the batched solve launch (portable)

@@ -380,6 +380,34 @@ __global__ void k_matvec64(const Inst *__restrict__ pI, const double *in, double
   out[3 * i + 2] = a2;
 }
 
+// batch state transfer: rows of all instances concatenated in table order, offs[k] = first row of
+// instance k (offs[n] = total); pack: SoA x, v of every instance -> AoS [rows][3] x then v; unpack: reverse
+__device__ inline int find_inst(const long long *offs, int n, long long row) {
+  int lo = 0, hi = n;   // largest k with offs[k] <= row
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (offs[mid] <= row) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+__global__ void k_pack_states(const Inst *__restrict__ insts, int n, const long long *__restrict__ offs, double *x,
+                              double *v, int unpack) {
+  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= offs[n]) return;
+  const int k = find_inst(offs, n, row);
+  const Inst &I = insts[k];
+  const int i = (int)(row - offs[k]);
+  for (int c = 0; c < 3; ++c) {
+    if (unpack) {
+      I.x[c * I.nv + i] = x[3 * row + c];
+      I.v[c * I.nv + i] = v[3 * row + c];
+    } else {
+      x[3 * row + c] = I.x[c * I.nv + i];
+      v[3 * row + c] = I.v[c * I.nv + i];
+    }
+  }
+}
+
 __global__ void k_aos_to_soa(const double *src, double *dst, int nv) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
@@ -429,6 +457,13 @@ cudaError_t launch_energy_reduce(const Inst *d, const Inst &h, double *out4, cud
 
 cudaError_t launch_matvec64(const Inst *d, const Inst &h, const double *in, double *out, cudaStream_t st) {
   k_matvec64<<<(h.nv + 255) / 256, 256, 0, st>>>(d, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_states(const Inst *d_insts, int n, const long long *d_offs, long long rows, double *d_x,
+                               double *d_v, int unpack, cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  k_pack_states<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(d_insts, n, d_offs, d_x, d_v, unpack);
   return cudaGetLastError();
 }
 

@@ -267,3 +267,24 @@ def test_autotune_changes_speed_not_results():
         gb.shell_batch_destroy(b)
     for (xa, va), (xb, vb) in zip(*out):
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_batch_packed_states_roundtrip():
+    """shell_batch_get/set_states move every resident instance's state in one packed copy each way, in slot
+    order, identical to the per-handle transfers."""
+    scs = sg.mixed_batch(5, seed=33, side_lo=4, side_hi=20)
+    b = gb.shell_batch_create(1 << 40)
+    hs = [gb.create_from_scenario(sc, precision="fp32_refine") for sc in scs]
+    for h in hs:
+        gb.shell_batch_admit(b, h)
+    gb.shell_batch_step(b, 2)
+    slots, offs = gb.shell_batch_state_layout(b)
+    x, v = gb.shell_batch_get_states(b)
+    for k, slot in enumerate(slots):
+        xa, va = gb.shell_get_state(b.members[int(slot)])
+        assert np.array_equal(x[offs[k]:offs[k + 1]], xa) and np.array_equal(v[offs[k]:offs[k + 1]], va)
+    gb.shell_batch_set_states(b, x + 0.25, v * 2.0)
+    for k, slot in enumerate(slots):
+        xa, va = gb.shell_get_state(b.members[int(slot)])
+        assert np.array_equal(xa, x[offs[k]:offs[k + 1]] + 0.25) and np.array_equal(va, v[offs[k]:offs[k + 1]] * 2.0)
+    gb.shell_batch_destroy(b)
