@@ -130,6 +130,9 @@ typedef struct shell_options {
   shell_free_fn free;
   void *alloc_user;
   int32_t preconditioner;  /* shell_preconditioner */
+  int32_t no_staging;      /* 0 (default): FP32 products stage each 256-row block's gathered vector entries in
+                            * shared memory when they fit; 1: gather from global memory. Results are bitwise
+                            * identical either way (same values, same order of operations); for measurement. */
 } shell_options;
 
 /* Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the

@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshells.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 CU = ["kernels_setup.cu", "kernels_force.cu", "kernels_solve.cu"]
-CPP = ["host_mesh.cpp", "amg_setup.cpp", "api.cpp"]
+CPP = ["host_mesh.cpp", "amg_setup.cpp", "halo.cpp", "api.cpp"]
 
 
 def cuda_home() -> str:

@@ -79,7 +79,7 @@ class shell_options(C.Structure):
     _fields_ = [("dt", C.c_double), ("precision", C.c_int32), ("pcg_rtol", C.c_double),
                 ("refine_rtol", C.c_double), ("pcg_max_it", C.c_int32), ("refine_max", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("preconditioner", C.c_int32)]
+                ("preconditioner", C.c_int32), ("no_staging", C.c_int32)]
 
 
 class shell_step_stats(C.Structure):
@@ -198,7 +198,7 @@ def _current_stream():
 
 def make_options(dt=1e-2, precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
                  stream: Optional[int] = None, use_torch_allocator: bool = True,
-                 preconditioner="auto") -> shell_options:
+                 preconditioner="auto", no_staging: bool = False) -> shell_options:
     lib = load_library()
     o = shell_options()
     lib.shell_default_options(C.byref(o))
@@ -209,6 +209,7 @@ def make_options(dt=1e-2, precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_m
     o.pcg_max_it = int(pcg_max_it)
     o.refine_max = int(refine_max)
     o.preconditioner = PRECONDITIONERS[preconditioner] if isinstance(preconditioner, str) else int(preconditioner)
+    o.no_staging = 1 if no_staging else 0
     o.cuda_stream = _current_stream() if stream is None else int(stream)
     hooks = _torch_allocator() if use_torch_allocator else None
     if hooks:
@@ -251,7 +252,7 @@ class Handle:
 def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None, init_vel=None, pinned=None,
                  clamped_edges=None, gravity=(0.0, 0.0, 0.0), load_vtx=None, load_f=None, dt=1e-2,
                  precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
-                 stream=None, use_torch_allocator=True, preconditioner="auto") -> Handle:
+                 stream=None, use_torch_allocator=True, preconditioner="auto", no_staging=False) -> Handle:
     """shell_create: rest-state precompute and constant-matrix assembly on the GPU (see include/shell.h)."""
     lib = load_library()
     tris = _arr(tris, np.int32, (-1, 3))
@@ -274,7 +275,7 @@ def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None,
     bc.load_vtx = _ptr(lv) if lv.shape[0] else None
     bc.load_f = _ptr(lf) if lv.shape[0] else None
     opts = make_options(dt, precision, pcg_rtol, refine_rtol, pcg_max_it, refine_max, stream, use_torch_allocator,
-                        preconditioner)
+                        preconditioner, no_staging)
     out = C.c_void_p()
     m = MODELS[model] if isinstance(model, str) else int(model)
     _check(lib.shell_create(C.byref(mesh), C.byref(mat), m, C.byref(bc), C.byref(opts), C.byref(out)), "shell_create")

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "amg_setup.h"
+#include "halo.h"
 #include "host_mesh.h"
 #include "internal.h"
 
@@ -82,6 +83,26 @@ struct Carver {
     return p;
   }
 };
+
+// gather lists of one matrix: device arrays carved from a block, then uploaded
+void halo_take(Carver &C, const HostHalo &H, HaloDev &D) {
+  D = HaloDev{};
+  if (H.ptr.empty()) return;
+  D.ptr = C.take<int32_t>(H.ptr.size());
+  D.col = C.take<int32_t>(H.col.size());
+  D.own = C.take<int32_t>(H.own.size());
+  D.c16 = C.take<uint16_t>(H.c16.size());
+  D.max = H.max;
+}
+
+cudaError_t halo_upload(const HostHalo &H, const HaloDev &D, cudaStream_t st) {
+  if (H.ptr.empty()) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(D.ptr, H.ptr.data(), 4 * H.ptr.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(D.col, H.col.data(), 4 * H.col.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(D.own, H.own.data(), 4 * H.own.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  return cudaMemcpyAsync(D.c16, H.c16.data(), 2 * H.c16.size(), cudaMemcpyHostToDevice, st);
+}
 
 }  // namespace
 
@@ -655,7 +676,7 @@ std::vector<double> to_soa(const double *aos, int nv) {
 
 // Multigrid preconditioner: download the assembled FP64 matrix, build the smoothed-aggregation hierarchy
 // on the host (the matrix is constant, so this happens once) and upload it as SELL-32 levels.
-int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
+int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   Inst &I = h->h;
   cudaStream_t st = h->mem.st;
   if (mode == SHELL_PRECOND_JACOBI) return SHELL_OK;
@@ -707,6 +728,17 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
       Rs[l] = to_sell(H.levels[l].R);
     }
   }
+  // gather lists for the FP32 products (level 0 shares the instance's)
+  const bool stage32 = stage && I.precision != SHELL_FP64;
+  std::vector<HostHalo> Ha(L), Hp(L), Hr(L);
+  for (int l = 0; stage32 && l < L; ++l) {
+    const HostAmgLevel &V = H.levels[l];
+    if (l > 0) build_halo(V.A.n, V.A.n, As[l].sl_ptr, As[l].sl_col, V.A.ptr, true, &Ha[l]);
+    if (l < L - 1) {
+      build_halo(V.P.n, V.P.m, Ps[l].sl_ptr, Ps[l].sl_col, V.P.ptr, false, &Hp[l]);
+      build_halo(V.R.n, V.R.m, Rs[l].sl_ptr, Rs[l].sl_col, V.R.ptr, false, &Hr[l]);
+    }
+  }
   const int nc = H.levels[L - 1].A.n;
   std::vector<AmgDev> lev(L);
   double *cinv64 = nullptr;
@@ -736,6 +768,12 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
         D.dinv32 = I.dinv32;
         D.dinv64 = I.dinv64;
       }
+      if (l > 0)
+        halo_take(C, Ha[l], D.ha);
+      else
+        D.ha = I.h0;
+      halo_take(C, Hp[l], D.hp);
+      halo_take(C, Hr[l], D.hr);
       if (l < L - 1) {
         D.p_ptr = C.take<int32_t>(Ps[l].sl_ptr.size());
         D.p_col = C.take<int32_t>(Ps[l].sl_col.size());
@@ -792,6 +830,9 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode) {
       CK(up(D.r_val64, Rs[l].val.data(), 8 * Rs[l].val.size()));
       CK(up(D.r_val32, f32(Rs[l].val), 4 * Rs[l].val.size()));
     }
+    if (l > 0) CK(halo_upload(Ha[l], D.ha, st));
+    CK(halo_upload(Hp[l], D.hp, st));
+    CK(halo_upload(Hr[l], D.hr, st));
     CK(cudaMemsetAsync(D.b, 0, 32 * (size_t)D.n, st));
     CK(cudaMemsetAsync(D.x, 0, 32 * (size_t)D.n, st));
     CK(cudaMemsetAsync(D.r, 0, 32 * (size_t)D.n, st));
@@ -919,6 +960,9 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   const int ne = T.ne;
   const int n_loads = bc ? bc->n_loads : 0;
 
+  HostHalo H0;   // gather lists of the matrix for the FP32 products
+  if (I.precision != SHELL_FP64 && !opt.no_staging) build_halo(nv, nv, T.sl_ptr, T.sl_col, T.row_ptr, true, &H0);
+
   for (int s0 = 0; s0 < nt; s0 += kForceBlock) h->tiles.push_back({0, 0, s0, std::min(kForceBlock, nt - s0)});
   for (int s0 = 0; s0 < ne; s0 += kForceBlock) h->tiles.push_back({0, 1, s0, std::min(kForceBlock, ne - s0)});
 
@@ -967,6 +1011,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.dinv32 = C.take<float>(nv);
     I.rs32 = C.take<float>(nv);
     I.diag_pos = C.take<int32_t>(nv);
+    halo_take(C, H0, I.h0);
     I.b = C.take<double>(3 * (size_t)nv);
     I.sol = C.take<double>(3 * (size_t)nv);
     I.r64 = C.take<double>(3 * (size_t)nv);
@@ -1061,6 +1106,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   CKF(up(I.sl_ptr, T.sl_ptr.data(), 4 * T.sl_ptr.size()));
   CKF(up(I.sl_col, T.sl_col.data(), 4 * T.sl_col.size()));
   CKF(up(I.diag_pos, T.diag_pos.data(), 4 * T.diag_pos.size()));
+  CKF(halo_upload(H0, I.h0, st));
   CKF(up(I.asm_ptr, T.asm_ptr.data(), 4 * T.asm_ptr.size()));
   CKF(up(I.asm_src, T.asm_src.data(), 4 * T.asm_src.size()));
   if (n_loads) {
@@ -1096,7 +1142,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     return (flags & 1) ? SHELL_ERR_DEGENERATE : SHELL_ERR_SINGULAR_OPERATOR;
   }
 #undef CKF
-  rc = setup_amg(h, T, opt.preconditioner);
+  rc = setup_amg(h, T, opt.preconditioner, !opt.no_staging);
   if (rc != SHELL_OK) {
     if (h->amg_block) h->mem.put(h->amg_block, h->amg_bytes);
     h->mem.put(h->block, h->block_bytes);

@@ -1,0 +1,55 @@
+// halo.cpp -- per-block gather lists of a SELL-32 matrix (see halo.h).
+#include "halo.h"
+
+#include <algorithm>
+
+namespace shl {
+
+bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, const std::vector<int32_t> &sl_col,
+                const std::vector<int32_t> &row_ptr, bool square, HostHalo *out) {
+  *out = HostHalo();
+  if (n_rows <= 0 || n_cols <= 0) return false;
+  const int n_blocks = (n_rows + kHaloBlock - 1) / kHaloBlock;
+  HostHalo H;
+  H.ptr.assign(n_blocks + 1, 0);
+  H.own.assign(n_blocks, 0);
+  H.c16.assign(sl_col.size(), 0);
+  std::vector<int32_t> list;
+  for (int b = 0; b < n_blocks; ++b) {
+    const int r0 = b * kHaloBlock, r1 = std::min(n_rows, r0 + kHaloBlock);
+    list.clear();
+    for (int r = r0; r < r1; ++r) {
+      const int s = r / 32, l = r % 32;
+      const int len = row_ptr[r + 1] - row_ptr[r];
+      for (int k = 0; k < len; ++k) list.push_back(sl_col[sl_ptr[s] + 32 * k + l]);
+      if (square) list.push_back(r);
+    }
+    if (list.empty()) list.push_back(0);
+    std::sort(list.begin(), list.end());
+    list.erase(std::unique(list.begin(), list.end()), list.end());
+    if (list.size() > 65535) return false;
+    H.max = std::max(H.max, (int)list.size());
+    const int own = square ? (int)(std::lower_bound(list.begin(), list.end(), r0) - list.begin()) : 0;
+    H.own[b] = own;
+    for (int r = r0; r < r1; ++r) {
+      const int s = r / 32, l = r % 32;
+      const int len = row_ptr[r + 1] - row_ptr[r];
+      const int w = (sl_ptr[s + 1] - sl_ptr[s]) / 32;
+      for (int k = 0; k < w; ++k) {
+        const int pos = sl_ptr[s] + 32 * k + l;
+        int loc;
+        if (k < len)
+          loc = (int)(std::lower_bound(list.begin(), list.end(), sl_col[pos]) - list.begin());
+        else
+          loc = square ? own + (r - r0) : 0;
+        H.c16[pos] = (uint16_t)loc;
+      }
+    }
+    H.col.insert(H.col.end(), list.begin(), list.end());
+    H.ptr[b + 1] = (int32_t)H.col.size();
+  }
+  *out = std::move(H);
+  return true;
+}
+
+}  // namespace shl

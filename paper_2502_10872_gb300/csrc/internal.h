@@ -42,6 +42,15 @@ struct InstStatus {
   long long last_ns;    // device time of the last step's solve of this instance (right-hand side to commit)
 };
 
+// Per-block gather lists of a SELL-32 matrix (device pointers): block b = rows [256 b, 256 b + 256) stages the
+// vector entries col[ptr[b] .. ptr[b+1]) in shared memory; c16 is each stored entry's index into its block's
+// list; own[b] is the local index of the block's first row (square matrices). max = 0: no lists.
+struct HaloDev {
+  int32_t *ptr, *col, *own;
+  uint16_t *c16;
+  int32_t max, pad;
+};
+
 // One level of the smoothed-aggregation multigrid preconditioner (device pointers). Matrices are SELL-32:
 // A (this level's operator), P (rows of this level -> columns of the next) and R = P^T (rows of the next
 // level -> columns of this one). Level vectors are array-of-structures [n][4] in the solve precision.
@@ -61,6 +70,7 @@ struct AmgDev {
   double *r_val64;
   double omega;                  // damped-Jacobi weight
   void *b, *x, *r, *y;
+  HaloDev ha, hp, hr;            // gather lists of A, P and R (FP32 products)
 };
 
 // Per-instance device descriptor (lives in device memory; every pointer is a device pointer).
@@ -117,6 +127,7 @@ struct Inst {
   double *dinv64; float *dinv32; // [nv] inverse diagonal (Jacobi)
   float *rs32;                   // [nv] row sums of A (FP64 sum, rounded): FP32 SpMV in difference form
   int32_t *diag_pos;             // [nv]
+  HaloDev h0;                    // gather lists of the matrix (FP32 products)
   int32_t *asm_ptr, *asm_src;    // assembly sources of each SELL position
   double *local;                 // [n_local] per-stencil local matrix entries
 
@@ -166,6 +177,8 @@ struct Sched {
   int32_t *cluster_ok;   // [n_ctas / cluster] per-cluster barrier verdict (hierarchical teams)
   int32_t n_ctas;
   int32_t cluster;       // CTAs per cluster of the launch, 0 = no clusters
+  int32_t halo_cap;      // vector entries the launch's dynamic shared memory stages (set by launch_solve)
+  int32_t pad;
 };
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)

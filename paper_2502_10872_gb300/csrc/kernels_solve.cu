@@ -21,6 +21,7 @@
 // FP64 mode: one CG in FP64 from the warm start v, until ||r|| <= rtol ||b||.
 // FP32 refinement mode: r64 = b - A v in FP64 (FP64 matrix and vector); inner CG in FP32 on A d = r64 from
 // d = 0 to a relative tolerance; v += d; repeat until ||r64|| <= refine_rtol ||b||.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.h"
@@ -53,6 +54,7 @@ struct Team {
   int cluster;  // CTAs per cluster
   int *cluster_ok;
   unsigned long long t0;   // start of the current instance's solve (global timer, ns)
+  int cap;      // vector entries the dynamic shared memory can stage (0: no staging)
 };
 
 __device__ inline void cluster_barrier() {
@@ -315,6 +317,90 @@ __device__ inline void spmv_row(const Inst &I, const float *__restrict__ val, co
   }
 }
 
+// ------------------------------------------------------------------ staged FP32 products
+// A CTA processes 256 rows at a time. With gather lists (HaloDev), it first copies the vector entries its
+// rows reference into shared memory (mostly contiguous runs, one coalesced pass), then every nonzero reads
+// its gathered value from there through a 16-bit local index: one global request per distinct column of the
+// block instead of one per nonzero, and 2 instead of 4 bytes of column index per nonzero.
+extern __shared__ float4 sh_halo[];   // dynamic shared memory: Team::cap entries
+
+__device__ inline bool halo_on(const HaloDev &H, int cap) { return H.max > 0 && H.max <= cap; }
+
+// all threads of the CTA; vec is written by other CTAs of the launch, so it is read with coherent loads
+__device__ __forceinline__ void stage_halo(const HaloDev &H, int blk, const float4 *vec) {
+  __syncthreads();   // earlier readers of the buffer are done
+  const int b = H.ptr[blk], n = H.ptr[blk + 1] - b;
+  // two entries per thread and pass: both column loads, then both gathers, are in flight together
+  for (int k = threadIdx.x; k < n; k += 2 * kBlock) {
+    const int k2 = k + kBlock;
+    const int c0 = __ldg(H.col + b + k);
+    const int c1 = k2 < n ? __ldg(H.col + b + k2) : c0;
+    const float4 t0 = vec[c0];
+    const float4 t1 = vec[c1];
+    sh_halo[k] = t0;
+    if (k2 < n) sh_halo[k2] = t1;
+  }
+  __syncthreads();
+}
+
+// difference form (square matrix) from the staged vector; own = local index of row
+__device__ inline void sell_diff_sh(const int32_t *sp, const uint16_t *c16, const float *__restrict__ val,
+                                    const float *rs, int own, int row, float &ax, float &ay, float &az) {
+  constexpr int U = 8;
+  const int s = row >> 5, lane = row & 31;
+  const int b1 = sp[s + 1];
+  const float4 ui = sh_halo[own];
+  const float r = rs[row];
+  ax = r * ui.x;
+  ay = r * ui.y;
+  az = r * ui.z;
+  for (int p = sp[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    float a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? (int)c16[q] : own;
+      a[j] = ok ? val[q] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const float4 t = sh_halo[c[j]];
+      ax += a[j] * (t.x - ui.x);
+      ay += a[j] * (t.y - ui.y);
+      az += a[j] * (t.z - ui.z);
+    }
+  }
+}
+
+// plain y_i = sum_j m_ij v_j from the staged vector
+__device__ inline void sell_plain_sh(const int32_t *sp, const uint16_t *c16, const float *__restrict__ val, int row,
+                                     float &ax, float &ay, float &az) {
+  constexpr int U = 8;
+  const int s = row >> 5, lane = row & 31;
+  const int b1 = sp[s + 1];
+  ax = ay = az = 0.0f;
+  for (int p = sp[s] + lane; p < b1; p += 32 * U) {
+    int c[U];
+    float a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? (int)c16[q] : 0;
+      a[j] = ok ? val[q] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const float4 t = sh_halo[c[j]];
+      ax += a[j] * t.x;
+      ay += a[j] * t.y;
+      az += a[j] * t.z;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ phases
 #define ROWS_BEGIN(I, tm)                                                                 \
   for (int ch = (tm).rank; ch < (I).n_chunks; ch += (tm).size) {                        \
@@ -411,18 +497,37 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
   const typename Vec<R>::G *g = Vec<R>::g(I);
   const R *r = reinterpret_cast<const R *>(I.r);
   R *w = reinterpret_cast<R *>(I.w);
+  bool st = false;
+  if constexpr (sizeof(R) == 4) st = halo_on(I.h0, tm.cap);
   ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
     R gu = R(0), wu = R(0), rr2 = R(0);
     for (int rr = 0; rr < I.rows_per_thread; ++rr) {
-      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
-      if (row >= nv) continue;
+      const int blk = ch * I.rows_per_thread + rr;
+      if (blk * kBlock >= nv) break;
       R ax, ay, az;
-      spmv_row(I, val, g, row, ax, ay, az);
+      typename Vec<R>::G u;
+      const int row = blk * kBlock + (int)threadIdx.x;
+      if constexpr (sizeof(R) == 4) {
+        if (st) {
+          stage_halo(I.h0, blk, g);
+          if (row >= nv) continue;
+          const int own = __ldg(I.h0.own + blk) + (int)threadIdx.x;
+          sell_diff_sh(I.sl_ptr, I.h0.c16, val, I.rs32, own, row, ax, ay, az);
+          u = sh_halo[own];
+        } else {
+          if (row >= nv) continue;
+          spmv_row(I, val, g, row, ax, ay, az);
+          u = ldg4(g + row);
+        }
+      } else {
+        if (row >= nv) continue;
+        spmv_row(I, val, g, row, ax, ay, az);
+        u = ldg4(g + row);
+      }
       w[row] = ax;
       w[nv + row] = ay;
       w[2 * nv + row] = az;
-      const typename Vec<R>::G u = ldg4(g + row);
       const R r0 = r[row], r1 = r[nv + row], r2 = r[2 * nv + row];
       gu += r0 * R(u.x) + r1 * R(u.y) + r2 * R(u.z);
       wu += ax * R(u.x) + ay * R(u.y) + az * R(u.z);
@@ -566,6 +671,121 @@ __device__ inline void level_a(const AmgDev &L, const D4 *v, int row, double &ax
 #define LEVEL_ROWS_END \
   }                    \
   }
+// Row phases of one level, each instantiated with and without shared-memory staging (ST; FP32 only), so
+// that a launch's loop carries only the live values of the path it takes.
+template <bool ST, typename G>
+__device__ inline void stage_blk(const HaloDev &H, int blk, const G *vec) {
+  if constexpr (ST) stage_halo(H, blk, vec);
+}
+template <bool ST>
+__device__ inline void level_a_st(const AmgDev &L, const float4 *v, int blk, int row, float &ax, float &ay, float &az) {
+  if constexpr (ST)
+    sell_diff_sh(L.a_ptr, L.ha.c16, L.a_val32, L.rs32, __ldg(L.ha.own + blk) + (int)threadIdx.x, row, ax, ay, az);
+  else
+    level_a(L, v, row, ax, ay, az);
+}
+template <bool ST>
+__device__ inline void level_a_st(const AmgDev &L, const D4 *v, int, int row, double &ax, double &ay, double &az) {
+  level_a(L, v, row, ax, ay, az);
+}
+template <bool ST>
+__device__ inline void plain_st(const int32_t *sp, const int32_t *sc, const uint16_t *c16, const float *sv,
+                                const float4 *v, int row, float &ax, float &ay, float &az) {
+  if constexpr (ST)
+    sell_plain_sh(sp, c16, sv, row, ax, ay, az);
+  else
+    sell_plain<float, float4>(sp, sc, sv, v, row, ax, ay, az);
+}
+template <bool ST>
+__device__ inline void plain_st(const int32_t *sp, const int32_t *sc, const uint16_t *, const double *sv, const D4 *v,
+                                int row, double &ax, double &ay, double &az) {
+  sell_plain<double, D4>(sp, sc, sv, v, row, ax, ay, az);
+}
+
+// residual of level l: r = b - A x
+template <typename R, bool ST>
+__device__ void lv_resid(const AmgDev &A, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const G *b = reinterpret_cast<const G *>(A.b);
+  const G *x = reinterpret_cast<const G *>(A.x);
+  G *rr = reinterpret_cast<G *>(A.r);
+  for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
+    stage_blk<ST>(A.ha, ch, x);
+    const int row = ch * kBlock + (int)threadIdx.x;
+    if (row >= A.n) continue;
+    R ax, ay, az;
+    level_a_st<ST>(A, x, ch, row, ax, ay, az);
+    const G bi = ldg4(b + row);
+    rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
+  }
+}
+
+// restriction to level l+1 with its pre-smoothing from zero fused: bc = R r; xc = omega_c Dc^-1 bc
+template <typename R, bool ST>
+__device__ void lv_restrict(const AmgDev &A, const AmgDev &C, bool pre, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const G *rr = reinterpret_cast<const G *>(A.r);
+  G *bc = reinterpret_cast<G *>(C.b);
+  G *xc = reinterpret_cast<G *>(C.x);
+  const R *dinvc = LevelVal<R>::dinv(C);
+  const R omc = R(C.omega);
+  for (int ch = tm.rank; ch * kBlock < A.n_next; ch += tm.size) {
+    stage_blk<ST>(A.hr, ch, rr);
+    const int row = ch * kBlock + (int)threadIdx.x;
+    if (row >= A.n_next) continue;
+    R ax, ay, az;
+    plain_st<ST>(A.r_ptr, A.r_col, A.hr.c16, LevelVal<R>::r(A), rr, row, ax, ay, az);
+    bc[row] = Vec<R>::mk(ax, ay, az);
+    if (pre) {
+      const R d = omc * dinvc[row];
+      xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
+    }
+  }
+}
+
+// coarse correction: x += P yc
+template <typename R, bool ST>
+__device__ void lv_prolong(const AmgDev &A, const AmgDev &C, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  G *x = reinterpret_cast<G *>(A.x);
+  const G *yc = reinterpret_cast<const G *>(C.y);
+  for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
+    stage_blk<ST>(A.hp, ch, yc);
+    const int row = ch * kBlock + (int)threadIdx.x;
+    if (row >= A.n) continue;
+    R ax, ay, az;
+    plain_st<ST>(A.p_ptr, A.p_col, A.hp.c16, LevelVal<R>::p(A), yc, row, ax, ay, az);
+    const G xi = ldg4(x + row);
+    x[row] = Vec<R>::mk(R(xi.x) + ax, R(xi.y) + ay, R(xi.z) + az);
+  }
+}
+
+// post-smoothing: y = x + omega D^-1 (b - A x)
+template <typename R, bool ST>
+__device__ void lv_smooth(const AmgDev &A, typename Vec<R>::G *y, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const G *b = reinterpret_cast<const G *>(A.b);
+  const G *x = reinterpret_cast<const G *>(A.x);
+  const R *dinv = LevelVal<R>::dinv(A);
+  const R om = R(A.omega);
+  for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
+    stage_blk<ST>(A.ha, ch, x);
+    const int row = ch * kBlock + (int)threadIdx.x;
+    if (row >= A.n) continue;
+    R ax, ay, az;
+    level_a_st<ST>(A, x, ch, row, ax, ay, az);
+    const G bi = ldg4(b + row);
+    const G xi = ldg4(x + row);
+    const R d = om * dinv[row];
+    y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+  }
+}
+
+// staging applies to FP32 products whose lists fit the launch's buffer
+template <typename R>
+__device__ inline bool staged(const HaloDev &H, int cap) {
+  return sizeof(R) == 4 && halo_on(H, cap);
+}
 
 // Pre-smoothing of level 0 from zero, row-local: b0 = r, x0 = omega D0^-1 r. It runs right after the phase
 // that wrote r for these rows (same thread), so it needs no barrier of its own.
@@ -598,31 +818,17 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
   // ---- down
   for (int l = 0; l < L - 1; ++l) {
     const AmgDev &A = I.amg[l];
-    G *b = reinterpret_cast<G *>(A.b);
-    G *x = reinterpret_cast<G *>(A.x);
-    G *rr = reinterpret_cast<G *>(A.r);
-    LEVEL_ROWS_BEGIN(A.n, tm)
-    R ax, ay, az;
-    level_a(A, x, row, ax, ay, az);
-    const G bi = ldg4(b + row);
-    rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
-    LEVEL_ROWS_END
+    if (staged<R>(A.ha, tm.cap))
+      lv_resid<R, (sizeof(R) == 4)>(A, tm);
+    else
+      lv_resid<R, false>(A, tm);
     if (!team_sync(tm)) return false;
     const AmgDev &C = I.amg[l + 1];
-    G *bc = reinterpret_cast<G *>(C.b);
-    G *xc = reinterpret_cast<G *>(C.x);
-    const R *dinvc = LevelVal<R>::dinv(C);
-    const R omc = R(C.omega);
     const bool pre = l + 1 < L - 1;   // the coarsest level is solved, not smoothed
-    LEVEL_ROWS_BEGIN(A.n_next, tm)
-    R ax, ay, az;
-    sell_plain<R, G>(A.r_ptr, A.r_col, LevelVal<R>::r(A), rr, row, ax, ay, az);
-    bc[row] = Vec<R>::mk(ax, ay, az);
-    if (pre) {
-      const R d = omc * dinvc[row];
-      xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
-    }
-    LEVEL_ROWS_END
+    if (staged<R>(A.hr, tm.cap))
+      lv_restrict<R, (sizeof(R) == 4)>(A, C, pre, tm);
+    else
+      lv_restrict<R, false>(A, C, pre, tm);
     if (!team_sync(tm)) return false;
   }
   // ---- coarsest
@@ -679,27 +885,17 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
   // ---- up
   for (int l = L - 2; l >= 0; --l) {
     const AmgDev &A = I.amg[l];
-    const G *b = reinterpret_cast<const G *>(A.b);
-    G *x = reinterpret_cast<G *>(A.x);
-    const G *yc = reinterpret_cast<const G *>(I.amg[l + 1].y);
-    LEVEL_ROWS_BEGIN(A.n, tm)
-    R ax, ay, az;
-    sell_plain<R, G>(A.p_ptr, A.p_col, LevelVal<R>::p(A), yc, row, ax, ay, az);
-    const G xi = ldg4(x + row);
-    x[row] = Vec<R>::mk(R(xi.x) + ax, R(xi.y) + ay, R(xi.z) + az);
-    LEVEL_ROWS_END
+    const AmgDev &C = I.amg[l + 1];
+    if (staged<R>(A.hp, tm.cap))
+      lv_prolong<R, (sizeof(R) == 4)>(A, C, tm);
+    else
+      lv_prolong<R, false>(A, C, tm);
     if (!team_sync(tm)) return false;
     G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
-    const R *dinv = LevelVal<R>::dinv(A);
-    const R om = R(A.omega);
-    LEVEL_ROWS_BEGIN(A.n, tm)
-    R ax, ay, az;
-    level_a(A, x, row, ax, ay, az);
-    const G bi = ldg4(b + row);
-    const G xi = ldg4(x + row);
-    const R d = om * dinv[row];
-    y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
-    LEVEL_ROWS_END
+    if (staged<R>(A.ha, tm.cap))
+      lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
+    else
+      lv_smooth<R, false>(A, y, tm);
     if (!team_sync(tm)) return false;
   }
   return true;
@@ -896,6 +1092,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
   tm.bank = 0;
   tm.cluster = sch.cluster;
   tm.cluster_ok = sch.cluster_ok;
+  tm.cap = sch.halo_cap;
   if (tm.size == 1)
     tm.mode = 0;
   else if (sch.cluster > 0 && tm.size % sch.cluster == 0)
@@ -931,9 +1128,32 @@ static SolveFn solve_fn(int prec, int occ) {
   return k_solve<0, 2>;
 }
 
+// Entries of the shared-memory staging buffer per CTA: as many as fit beside the static shared memory at the
+// variant's CTAs per SM (228 KB per SM, 1 KB reserved per CTA). FP64-only launches stage nothing.
+int solve_halo_cap(int prec, int occ) {
+  if (prec == 1) return 0;
+  if (prec == 2 && occ >= 5) return 2048;
+  if (prec == 2 && occ == 4) return 3072;
+  return 4096;
+}
+
+static cudaError_t prepare_solve_fn(int prec, int occ) {
+  static bool done[3][6];
+  const int o = std::min(5, std::max(0, occ));
+  if (done[prec][o]) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(solve_fn(prec, occ), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       16 * solve_halo_cap(prec, occ));
+  if (e == cudaSuccess) done[prec][o] = true;
+  return e;
+}
+
 int solve_blocks_per_sm(int prec, int occ) {
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_fn(prec, occ), kBlock, 0);
+  if (prepare_solve_fn(prec, occ) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, solve_fn(prec, occ), kBlock, 16 * solve_halo_cap(prec, occ));
   return n;
 }
 
@@ -941,10 +1161,14 @@ int solve_blocks_per_sm(int prec, int occ) {
 // whole cluster (hardware co-schedules a cluster, and no team waits for CTAs outside its cluster); teams
 // larger than a cluster need the cooperative launch (all CTAs co-resident) and use global barriers.
 cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, int occ, cudaStream_t st) {
+  cudaError_t e = prepare_solve_fn(prec, occ);
+  if (e != cudaSuccess) return e;
+  Sched sc = sched;
+  sc.halo_cap = solve_halo_cap(prec, occ);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = 16 * (size_t)sc.halo_cap;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   if (sched.cluster > 0) {
@@ -958,7 +1182,7 @@ cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int 
   }
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, solve_fn(prec, occ), d_insts, sched);
+  return cudaLaunchKernelEx(&cfg, solve_fn(prec, occ), d_insts, sc);
 }
 
 int solve_max_clusters(int prec, int cluster) {
@@ -972,8 +1196,10 @@ int solve_max_clusters(int prec, int cluster) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  cfg.dynamicSmemBytes = 16 * (size_t)solve_halo_cap(prec, 3);
   int n = 0;
-  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, solve_fn(prec, 3), &cfg);
+  cudaError_t e = prepare_solve_fn(prec, 3);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, solve_fn(prec, 3), &cfg);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
