@@ -844,6 +844,13 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   I.amg_levels = L;
   I.amg_coarse_n = nc;
   I.amg_coarse_sweeps = H.coarse_sweeps;
+  // agglomeration: the first level of at most one block of rows (classic phase structure without staging)
+  I.amg_agg = L;
+  for (int l = 1; stage && l < L; ++l)
+    if (H.levels[l].A.n <= kBlock) {
+      I.amg_agg = l;
+      break;
+    }
   I.amg = d_lev;
   I.amg_cinv64 = cinv64;
   I.amg_cinv32 = cinv32;

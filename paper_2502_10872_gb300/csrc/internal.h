@@ -149,7 +149,7 @@ struct Inst {
   int32_t amg_levels;
   int32_t amg_coarse_n;          // rows of the coarsest level
   int32_t amg_coarse_sweeps;     // 0: dense inverse on the coarsest level, else Jacobi sweeps
-  int32_t pad1;
+  int32_t amg_agg;               // first level a multi-CTA team hands to its rank-0 CTA (amg_levels: none)
   AmgDev *amg;                   // [amg_levels]
   double *amg_cinv64;            // dense inverse of the coarsest operator [n][n]
   float *amg_cinv32;

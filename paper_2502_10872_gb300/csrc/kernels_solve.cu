@@ -807,97 +807,135 @@ __device__ void vcycle_pre0(const Inst &I, const Team &tm) {
   LEVEL_ROWS_END
 }
 
+// One level of the down sweep: residual, then restriction (with the next level's pre-smoothing fused).
+template <typename R>
+__device__ bool down_resid(const Inst &I, int l, const Team &tm) {
+  const AmgDev &A = I.amg[l];
+  if (staged<R>(A.ha, tm.cap))
+    lv_resid<R, (sizeof(R) == 4)>(A, tm);
+  else
+    lv_resid<R, false>(A, tm);
+  return team_sync(tm);
+}
+template <typename R>
+__device__ bool down_restrict(const Inst &I, int l, const Team &tm) {
+  const AmgDev &A = I.amg[l];
+  const AmgDev &C = I.amg[l + 1];
+  const bool pre = l + 1 < I.amg_levels - 1;   // the coarsest level is solved, not smoothed
+  if (staged<R>(A.hr, tm.cap))
+    lv_restrict<R, (sizeof(R) == 4)>(A, C, pre, tm);
+  else
+    lv_restrict<R, false>(A, C, pre, tm);
+  return team_sync(tm);
+}
+
+// coarsest level: y = C^-1 b (dense inverse) or damped-Jacobi sweeps from zero
+template <typename R>
+__device__ bool coarsest(const Inst &I, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const AmgDev &C = I.amg[I.amg_levels - 1];
+  const G *b = reinterpret_cast<const G *>(C.b);
+  G *y = reinterpret_cast<G *>(C.y);
+  if (I.amg_coarse_sweeps == 0) {
+    const R *ci = LevelVal<R>::cinv(I);
+    const int n = C.n;
+    LEVEL_ROWS_BEGIN(n, tm)
+    R ax = R(0), ay = R(0), az = R(0);
+    for (int j = 0; j < n; ++j) {
+      const R a = ci[(size_t)row * n + j];
+      const G t = ldg4(b + j);
+      ax += a * R(t.x);
+      ay += a * R(t.y);
+      az += a * R(t.z);
+    }
+    y[row] = Vec<R>::mk(ax, ay, az);
+    LEVEL_ROWS_END
+    return team_sync(tm);
+  }
+  G *x = reinterpret_cast<G *>(C.x);
+  const R *dinv = LevelVal<R>::dinv(C);
+  const R om = R(C.omega);
+  LEVEL_ROWS_BEGIN(C.n, tm)
+  const G bi = ldg4(b + row);
+  const R d = om * dinv[row];
+  y[row] = Vec<R>::mk(d * R(bi.x), d * R(bi.y), d * R(bi.z));
+  LEVEL_ROWS_END
+  if (!team_sync(tm)) return false;
+  for (int sw = 1; sw < I.amg_coarse_sweeps; ++sw) {
+    G *src = (sw & 1) ? y : x;
+    G *dst = (sw & 1) ? x : y;
+    LEVEL_ROWS_BEGIN(C.n, tm)
+    R ax, ay, az;
+    level_a(C, src, row, ax, ay, az);
+    const G bi = ldg4(b + row);
+    const G xi = ldg4(src + row);
+    const R d = om * dinv[row];
+    dst[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+  }
+  if ((I.amg_coarse_sweeps & 1) == 0) {   // the last sweep wrote x: move it to y
+    LEVEL_ROWS_BEGIN(C.n, tm)
+    y[row] = ldg4(x + row);
+    LEVEL_ROWS_END
+    if (!team_sync(tm)) return false;
+  }
+  return true;
+}
+
+// One level of the up sweep: coarse correction and post-smoothing; the output of level 0 is u (in g).
+template <typename R>
+__device__ bool up_level(const Inst &I, int l, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const AmgDev &A = I.amg[l];
+  const AmgDev &C = I.amg[l + 1];
+  G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
+  if (staged<R>(A.hp, tm.cap))
+    lv_prolong<R, (sizeof(R) == 4)>(A, C, tm);
+  else
+    lv_prolong<R, false>(A, C, tm);
+  if (!team_sync(tm)) return false;
+  if (staged<R>(A.ha, tm.cap))
+    lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
+  else
+    lv_smooth<R, false>(A, y, tm);
+  return team_sync(tm);
+}
+
 // u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing, Galerkin coarse operators and a dense
 // coarsest solve; output u in g (AoS). Expects vcycle_pre0 and a team barrier before it. The pre-smoothing
-// of each coarser level is fused into the restriction that produces its right-hand side. Returns false on
+// of each coarser level is fused into the restriction that produces its right-hand side.
+// Agglomeration: from level a = amg_agg on (at most one block of rows per level) a multi-CTA team hands the
+// cycle to its rank-0 CTA, which runs those phases alone with block barriers (the same products, so the
+// same values), while the other CTAs wait at one team barrier instead of one per phase. Returns false on
 // abort.
 template <typename R>
 __device__ bool vcycle(const Inst &I, const Team &tm) {
-  typedef typename Vec<R>::G G;
   const int L = I.amg_levels;
-  // ---- down
-  for (int l = 0; l < L - 1; ++l) {
-    const AmgDev &A = I.amg[l];
-    if (staged<R>(A.ha, tm.cap))
-      lv_resid<R, (sizeof(R) == 4)>(A, tm);
-    else
-      lv_resid<R, false>(A, tm);
-    if (!team_sync(tm)) return false;
-    const AmgDev &C = I.amg[l + 1];
-    const bool pre = l + 1 < L - 1;   // the coarsest level is solved, not smoothed
-    if (staged<R>(A.hr, tm.cap))
-      lv_restrict<R, (sizeof(R) == 4)>(A, C, pre, tm);
-    else
-      lv_restrict<R, false>(A, C, pre, tm);
-    if (!team_sync(tm)) return false;
-  }
-  // ---- coarsest
-  {
-    const AmgDev &C = I.amg[L - 1];
-    const G *b = reinterpret_cast<const G *>(C.b);
-    G *y = reinterpret_cast<G *>(C.y);
-    if (I.amg_coarse_sweeps == 0) {
-      const R *ci = LevelVal<R>::cinv(I);
-      const int n = C.n;
-      LEVEL_ROWS_BEGIN(n, tm)
-      R ax = R(0), ay = R(0), az = R(0);
-      for (int j = 0; j < n; ++j) {
-        const R a = ci[(size_t)row * n + j];
-        const G t = ldg4(b + j);
-        ax += a * R(t.x);
-        ay += a * R(t.y);
-        az += a * R(t.z);
+  const int a = (tm.size > 1 && I.amg_agg >= 1 && I.amg_agg < L) ? I.amg_agg : L;
+  for (int l = 0; l < a - 1; ++l)
+    if (!down_resid<R>(I, l, tm) || !down_restrict<R>(I, l, tm)) return false;
+  if (a < L) {
+    if (!down_resid<R>(I, a - 1, tm)) return false;
+    if (tm.rank == 0) {
+      Team lt = tm;
+      lt.rank = 0;
+      lt.size = 1;
+      lt.mode = 0;
+      down_restrict<R>(I, a - 1, lt);
+      for (int l = a; l < L - 1; ++l) {
+        down_resid<R>(I, l, lt);
+        down_restrict<R>(I, l, lt);
       }
-      y[row] = Vec<R>::mk(ax, ay, az);
-      LEVEL_ROWS_END
-      if (!team_sync(tm)) return false;
-    } else {
-      G *x = reinterpret_cast<G *>(C.x);
-      const R *dinv = LevelVal<R>::dinv(C);
-      const R om = R(C.omega);
-      LEVEL_ROWS_BEGIN(C.n, tm)
-      const G bi = ldg4(b + row);
-      const R d = om * dinv[row];
-      y[row] = Vec<R>::mk(d * R(bi.x), d * R(bi.y), d * R(bi.z));
-      LEVEL_ROWS_END
-      if (!team_sync(tm)) return false;
-      for (int sw = 1; sw < I.amg_coarse_sweeps; ++sw) {
-        G *src = (sw & 1) ? y : x;
-        G *dst = (sw & 1) ? x : y;
-        LEVEL_ROWS_BEGIN(C.n, tm)
-        R ax, ay, az;
-        level_a(C, src, row, ax, ay, az);
-        const G bi = ldg4(b + row);
-        const G xi = ldg4(src + row);
-        const R d = om * dinv[row];
-        dst[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
-        LEVEL_ROWS_END
-        if (!team_sync(tm)) return false;
-      }
-      if ((I.amg_coarse_sweeps & 1) == 0) {   // the last sweep wrote x: move it to y
-        LEVEL_ROWS_BEGIN(C.n, tm)
-        y[row] = ldg4(x + row);
-        LEVEL_ROWS_END
-        if (!team_sync(tm)) return false;
-      }
+      coarsest<R>(I, lt);
+      for (int l = L - 2; l >= a; --l) up_level<R>(I, l, lt);
     }
-  }
-  // ---- up
-  for (int l = L - 2; l >= 0; --l) {
-    const AmgDev &A = I.amg[l];
-    const AmgDev &C = I.amg[l + 1];
-    if (staged<R>(A.hp, tm.cap))
-      lv_prolong<R, (sizeof(R) == 4)>(A, C, tm);
-    else
-      lv_prolong<R, false>(A, C, tm);
     if (!team_sync(tm)) return false;
-    G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
-    if (staged<R>(A.ha, tm.cap))
-      lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
-    else
-      lv_smooth<R, false>(A, y, tm);
-    if (!team_sync(tm)) return false;
+  } else if (!coarsest<R>(I, tm)) {
+    return false;
   }
+  for (int l = (a < L ? a - 1 : L - 2); l >= 0; --l)
+    if (!up_level<R>(I, l, tm)) return false;
   return true;
 }
 
