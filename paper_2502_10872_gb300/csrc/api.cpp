@@ -246,18 +246,26 @@ int rebuild_tables(shell_batch *b) {
   const int CS = use_clusters ? kCluster : 0;
   int G = num_sms() * occ;
   if (CS) G = std::max(CS, std::min(G, max_clusters_cached(b->prec) * CS) / CS * CS);
-  // single-CTA-equivalent solve time of each instance: measured (last solve time x team size, corrected by
-  // the team-overhead model below) once the instance has run, else rows x iterations
-  constexpr double kBeta = 0.04;   // barrier overhead per extra CTA of a team: t(c) = w/c (1 + beta (c-1))
+  // Team-time model of an instance of B row blocks (chunks) on c CTAs: t(c) = w ceil(B/c)/B (1 + beta (c-1)).
+  // Every CTA of a team takes its share of whole blocks in each phase, so the phase ends with the CTAs that
+  // hold ceil(B/c) blocks: the time falls in steps, and the smallest c of a step is the one to use; beta is
+  // the barrier overhead per extra CTA. w (the one-CTA time) is measured (the last solve time, divided by
+  // the model's factor for the team it ran with) once the instance has run, else rows x iterations.
+  constexpr double kBeta = 0.04;
   const double beta = kBeta * b->share_scale;
+  auto cmax = [&](int k) { return std::max(1, b->slots[b->active[k]]->h.n_chunks); };
+  auto factor = [&](int k, int c) {
+    const double B = cmax(k);
+    return std::ceil(B / c) / B * (1.0 + beta * (c - 1));
+  };
   std::vector<double> work(n);
   bool measured = true;
   for (int k = 0; k < n; ++k) measured &= b->slots[b->active[k]]->meas_ns > 0;
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
     if (measured) {
-      const double c = std::max(1, h->meas_team);
-      work[k] = (double)h->meas_ns * c / (1.0 + beta * (c - 1.0));
+      const int c = std::max(1, std::min(cmax(k), h->meas_team));
+      work[k] = (double)h->meas_ns / factor(k, c);
     } else {
       work[k] = (double)h->nv * std::max(1.0, h->est_iters) * (h->h.amg_levels > 0 ? 6.0 : 1.0);
     }
@@ -269,8 +277,7 @@ int rebuild_tables(shell_batch *b) {
   std::vector<int> team_size, team_of(n, -1);
   std::vector<std::vector<int>> team_inst;
   int used = 0;
-  auto cmax = [&](int k) { return std::max(1, b->slots[b->active[k]]->h.n_chunks); };
-  auto t_of = [&](int k, int c) { return work[k] / c * (1.0 + beta * (c - 1)); };
+  auto t_of = [&](int k, int c) { return work[k] * factor(k, c); };
   if (CS) {
     // one-cluster teams for instances that want at least half a cluster, single CTAs for the rest
     double total = 0.0;
@@ -320,7 +327,9 @@ int rebuild_tables(shell_batch *b) {
     };
     double lo = 0.0, hi = 0.0;
     for (int k = 0; k < n; ++k) {
-      lo = std::max(lo, t_of(k, cmax(k)));
+      double best = t_of(k, 1);
+      for (int c = 2; c <= cmax(k); ++c) best = std::min(best, t_of(k, c));
+      lo = std::max(lo, best);
       hi += work[k];
     }
     if (plan(lo, nullptr, nullptr) > G) {
