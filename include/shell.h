@@ -258,7 +258,9 @@ int shell_batch_set_profiling(shell_batch *b, int32_t on);
 /* Autotune the persistent solve launch of this batch: flat teams (any size, global barriers, cooperative
  * launch) with 3 occupancies (CTAs per SM: 1, half, the maximum) x 3 CTA shares for large instances (x0.5,
  * x1, x2), and one-cluster teams (8-CTA thread-block clusters, hardware cluster barrier) with the 3 shares;
- * steps_per_trial real (committed) steps each; keeps the fastest by device time. A batch's results do not
+ * steps_per_trial real (committed) steps each; keeps the fastest by device time, then runs 3 more calls of
+ * steps_per_trial steps with it, re-planning the teams from that shape's own measured times (so a call takes
+ * (trials that ran + 3) x steps_per_trial committed steps). A batch's results do not
  * depend on the launch shape, so tuning changes only speed. out_ms: NULL or [12] mean step time of each trial
  * (-1 if skipped, -2 if it ran but the cluster launch was refused); out_choice: NULL or [3] = {CTAs per SM, share x 100, 1 if clusters}. */
 int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice);

@@ -461,8 +461,9 @@ def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:
     _check(load_library().shell_batch_autotune(b.ptr, int(steps_per_trial), ms.ctypes.data, choice.ctypes.data),
            "shell_batch_autotune")
     ran = int(np.sum(ms != -1.0))     # -1: skipped; -2: ran, cluster launch refused
+    settle = 3                        # calls with the chosen shape after the trials
     return {"trial_ms": ms.tolist(), "ctas_per_sm": int(choice[0]), "share_scale": choice[1] / 100.0,
-            "clusters": bool(choice[2]), "steps": ran * int(steps_per_trial)}
+            "clusters": bool(choice[2]), "steps": (ran + settle) * int(steps_per_trial)}
 
 
 def shell_batch_state_layout(b: Batch):

@@ -129,9 +129,15 @@ struct shell_handle {
   size_t amg_bytes = 0;
   int64_t vcycle_bytes = 0;      // algorithmic bytes of one FP32 V-cycle
   double est_iters = 64.0;       // scheduling estimate (PCG iterations per step)
-  long long meas_ns = 0;         // device solve time of the last step (0 = never run)
+  long long meas_ns = 0;         // longest device solve time of the last call's steps (0 = never run)
   int meas_team = 0;             // team size it ran with
-  double sched_est = 64.0;       // estimate the current schedule was planned with
+  // longest solve time, with its team size, of each of the last kHist calls: the schedule plans for the
+  // slowest of them, so that an instance whose step cost varies (one or two refinement rounds) is not
+  // given a team sized for its cheap steps
+  static constexpr int kHist = 4;
+  long long hist_ns[kHist] = {0, 0, 0, 0};
+  int hist_team[kHist] = {0, 0, 0, 0};
+  int hist_n = 0;
   int64_t nnz = 0, nnz_pad = 0;
   InstStatus last_status{};
 };
@@ -264,12 +270,14 @@ int rebuild_tables(shell_batch *b) {
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
     if (measured) {
-      const int c = std::max(1, std::min(cmax(k), h->meas_team));
-      work[k] = (double)h->meas_ns / factor(k, c);
+      work[k] = 0.0;
+      for (int q = 0; q < std::min(h->hist_n, shell_handle::kHist); ++q) {
+        const int c = std::max(1, std::min(cmax(k), h->hist_team[q]));
+        work[k] = std::max(work[k], (double)h->hist_ns[q] / factor(k, c));
+      }
     } else {
       work[k] = (double)h->nv * std::max(1.0, h->est_iters) * (h->h.amg_levels > 0 ? 6.0 : 1.0);
     }
-    h->sched_est = h->est_iters;
   }
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -585,13 +593,16 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       const double it = double(a.total_iters - z.total_iters + 2 * (a.total_rounds - z.total_rounds)) / done;
       h->est_iters = std::max(1.0, it);
       // results do not depend on the schedule, so re-plan freely when the work estimate moved: on the first
-      // measurement, and when the measured solve time leaves the planned makespan by more than 25 %
+      // measurement, and when the measured solve time leaves the planned makespan (below)
       const bool first_meas = h->meas_ns == 0;
-      h->meas_ns = a.last_ns;
+      h->meas_ns = std::max(a.max_ns, a.last_ns);
       h->meas_team = a.team_size;
+      h->hist_ns[h->hist_n % shell_handle::kHist] = h->meas_ns;
+      h->hist_team[h->hist_n % shell_handle::kHist] = a.team_size;
+      h->hist_n++;
       if (first_meas) b->dirty = true;
-      if (b->policy == 0 && b->plan_T > 0 && h->meas_ns > 1.25 * b->plan_T) b->dirty = true;
-      if (std::fabs(h->est_iters - h->sched_est) > 0.25 * h->sched_est) b->dirty = true;
+      // by more than the timing noise
+      if (b->policy == 0 && b->plan_T > 0 && h->meas_ns > 1.05 * b->plan_T) b->dirty = true;
     }
     if (stats) {
       shell_step_stats &o = stats[b->active[k]];
@@ -986,6 +997,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   auto layout = [&](Carver &C) {
     I.x = C.take<double>(3 * (size_t)nv);
     I.v = C.take<double>(3 * (size_t)nv);
+    I.vprev = C.take<double>(3 * (size_t)nv);
     I.rest = C.take<double>(3 * (size_t)nv);
     I.fext = C.take<double>(3 * (size_t)nv);
     I.mass = C.take<double>(nv);
@@ -1113,6 +1125,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   CKF(up(I.rest, rest.data(), 8 * rest.size()));
   CKF(up(I.x, x0.data(), 8 * x0.size()));
   CKF(up(I.v, v0.data(), 8 * v0.size()));
+  CKF(up(I.vprev, v0.data(), 8 * v0.size()));
   CKF(up(I.pinned, pin.data(), nv));
   CKF(up(I.t_idx, T.t_idx.data(), 4 * T.t_idx.size()));
   CKF(up(I.t_bc, T.t_bc.data(), T.t_bc.size()));
@@ -1285,6 +1298,7 @@ int shell_set_state(shell_handle *h, const double *x, const double *v) {
   if (v) {
     CK(cudaMemcpyAsync(h->d_stage + n3, v, 8 * n3, cudaMemcpyHostToDevice, st));
     CK(launch_aos_to_soa(h->d_stage + n3, h->h.v, h->nv, st));
+    CK(cudaMemcpyAsync(h->h.vprev, h->h.v, 8 * n3, cudaMemcpyDeviceToDevice, st));
   }
   // a new state clears a previous step failure
   CK(cudaMemsetAsync(&h->h.status->err, 0, sizeof(int32_t), st));
@@ -1305,7 +1319,10 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
   if (!h) return SHELL_ERR_INVALID_ARG;
   cudaStream_t st = h->mem.st;
   if (d_x) CK(launch_aos_to_soa(d_x, h->h.x, h->nv, st));
-  if (d_v) CK(launch_aos_to_soa(d_v, h->h.v, h->nv, st));
+  if (d_v) {
+    CK(launch_aos_to_soa(d_v, h->h.v, h->nv, st));
+    CK(cudaMemcpyAsync(h->h.vprev, h->h.v, 24 * (size_t)h->nv, cudaMemcpyDeviceToDevice, st));
+  }
   return SHELL_OK;
 }
 
@@ -1514,6 +1531,8 @@ int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n) {
 // Autotuner: the results of a batch do not depend on its launch shape (every reduction has a fixed order
 // independent of the team layout), so candidate shapes are tried on real, committed steps and timed with
 // CUDA events; the fastest is kept.
+constexpr int kSettleCalls = 3;   // calls of steps_per_trial steps after the trials (see include/shell.h)
+
 int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice) {
   if (!b || steps_per_trial < 1) return SHELL_ERR_INVALID_ARG;
   if (b->dirty) {
@@ -1557,6 +1576,21 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
   b->policy = best_k < 9 ? 0 : 1;
   b->occ = occs[best_k < 9 ? best_k / 3 : 2];
   b->share_scale = scales[best_k % 3];
+  // settle: the schedule of the chosen shape is planned from measured times, and those measured under the
+  // trials' other shapes predict it poorly; one call with the chosen shape replaces them, then further calls
+  // re-plan from the chosen shape's own times
+  for (int q = 0; q < kSettleCalls; ++q) {
+    b->dirty = true;
+    int rc = batch_step(b, steps_per_trial, nullptr);
+    if (rc != SHELL_OK) return rc;
+    if (q == 0)
+      for (int i : b->active) {
+        shell_handle *h = b->slots[i];
+        h->hist_ns[0] = h->meas_ns;
+        h->hist_team[0] = h->meas_team;
+        h->hist_n = 1;
+      }
+  }
   b->dirty = true;
   if (out_choice) {
     out_choice[0] = b->occ;

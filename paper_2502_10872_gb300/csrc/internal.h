@@ -40,6 +40,7 @@ struct InstStatus {
   int32_t team_size;    // CTAs that solved this instance in the last step
   long long total_rounds;
   long long last_ns;    // device time of the last step's solve of this instance (right-hand side to commit)
+  long long max_ns;     // longest solve time since the status was last gathered (the gather resets it)
 };
 
 // Per-block gather lists of a SELL-32 matrix (device pointers): block b = rows [256 b, 256 b + 256) stages the
@@ -90,6 +91,7 @@ struct Inst {
 
   // state (FP64, SoA [3][nv])
   double *x, *v, *rest, *fext;
+  double *vprev;                 // velocity before the last committed step (warm-start extrapolation)
   double *mass;                  // [nv]
   uint8_t *pinned;               // [nv]
 

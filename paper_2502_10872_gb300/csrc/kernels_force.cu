@@ -401,6 +401,7 @@ __global__ void k_pack_states(const Inst *__restrict__ insts, int n, const long 
     if (unpack) {
       I.x[c * I.nv + i] = x[3 * row + c];
       I.v[c * I.nv + i] = v[3 * row + c];
+      I.vprev[c * I.nv + i] = v[3 * row + c];
     } else {
       x[3 * row + c] = I.x[c * I.nv + i];
       v[3 * row + c] = I.v[c * I.nv + i];
@@ -422,7 +423,10 @@ __global__ void k_soa_to_aos(const double *src, double *dst, int nv) {
 __global__ void k_gather_status(const Inst *__restrict__ insts, int n, InstStatus *out, const int32_t *abort_flag,
                                 int32_t *out_abort) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) out[k] = *insts[k].status;
+  if (k < n) {
+    out[k] = *insts[k].status;
+    insts[k].status->max_ns = 0;
+  }
   if (k == 0) *out_abort = *abort_flag;
 }
 

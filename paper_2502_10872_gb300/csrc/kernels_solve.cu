@@ -412,7 +412,7 @@ __device__ inline void sell_plain_sh(const int32_t *sp, const uint16_t *c16, con
   }              \
   }
 
-// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = v; g64 = sol; partial ||b||^2
+// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = 2 v - v_prev; g64 = sol; partial ||b||^2
 template <typename RC>
 __device__ void phase_rhs(const Inst &I, const Team &tm) {
   const int nv = I.nv;
@@ -439,7 +439,8 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
         if (pin) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
-        sv[c] = pin ? 0.0 : v;
+        // initial guess: linear extrapolation of the last two velocities (v after a state is set)
+        sv[c] = pin ? 0.0 : 2.0 * v - I.vprev[c * nv + row];
         I.sol[c * nv + row] = sv[c];
       }
       reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
@@ -994,13 +995,14 @@ __device__ void phase_accumulate(const Inst &I, const Team &tm) {
   ROWS_END
 }
 
-// v = sol; x += dt v
+// v_prev = v; v = sol; x += dt v
 __device__ void phase_commit(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   ROWS_BEGIN(I, tm)
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
     const double v = I.sol[k];
+    I.vprev[k] = I.v[k];
     I.v[k] = v;
     I.x[k] += I.dt * v;
   }
@@ -1011,6 +1013,7 @@ __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, in
   if (tm.rank == 0 && threadIdx.x == 0) {
     InstStatus *s = I.status;
     s->last_ns = (long long)(gtimer() - tm.t0);
+    s->max_ns = s->last_ns > s->max_ns ? s->last_ns : s->max_ns;
     s->team_size = tm.size;
     if (err == SHELL_OK) {
       s->steps_done += 1;
