@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--launch", default=None,
+                    help="CTAS_PER_SM,SHARE,CLUSTERS: apply this solve-launch shape to the FP32 batch instead of "
+                         "autotuning (e.g. the shape a plain run chose, for a profiler run whose timings would "
+                         "mislead the autotuner); three settling calls of 2 steps replace the tuning trials")
+
     return ap.parse_args()
 
 
@@ -298,7 +303,13 @@ def main():
     tuned = {}
 
     def timed(b, K, W, profile, tune_key=None):
-        if tune_key is not None:
+        if tune_key == "fp32_refine" and args.launch:
+            c, sh, cl = args.launch.split(",")
+            gb.shell_batch_set_launch(b, int(c), float(sh), bool(int(cl)))
+            for _ in range(3):
+                gb.shell_batch_step(b, 2)
+            tuned[tune_key] = {"fixed": args.launch, "steps": 6}
+        elif tune_key is not None:
             # the autotuner runs real steps (part of the untimed warm-up); results do not depend on it
             tuned[tune_key] = gb.shell_batch_autotune(b, 2)
         gb.shell_batch_step(b, W)

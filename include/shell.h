@@ -264,6 +264,11 @@ int shell_batch_set_profiling(shell_batch *b, int32_t on);
  * depend on the launch shape, so tuning changes only speed. out_ms: NULL or [12] mean step time of each trial
  * (-1 if skipped, -2 if it ran but the cluster launch was refused); out_choice: NULL or [3] = {CTAs per SM, share x 100, 1 if clusters}. */
 int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms, int32_t *out_choice);
+/* Set the solve launch's shape without tuning, in the format of shell_batch_autotune's out_choice:
+ * ctas_per_sm (capped at the kernel variant's occupancy), share_x100 (CTA share of large instances x 100),
+ * clusters (1: one-cluster teams). For reusing a shape tuned earlier on the same workload. The teams are
+ * re-planned at the next step; results do not depend on the shape. Errors: INVALID_ARG. */
+int shell_batch_set_launch(shell_batch *b, int32_t ctas_per_sm, int32_t share_x100, int32_t clusters);
 int shell_batch_kernel_times(shell_batch *b, double out_ms[2]);
 int shell_batch_destroy(shell_batch *b);
 

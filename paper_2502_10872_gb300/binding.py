@@ -466,6 +466,12 @@ def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:
             "clusters": bool(choice[2]), "steps": (ran + settle) * int(steps_per_trial)}
 
 
+def shell_batch_set_launch(b: Batch, ctas_per_sm: int, share_scale: float = 1.0, clusters: bool = False):
+    """Apply a solve-launch shape without tuning (the fields shell_batch_autotune reports)."""
+    _check(load_library().shell_batch_set_launch(b.ptr, int(ctas_per_sm), int(round(share_scale * 100)),
+                                                 1 if clusters else 0), "shell_batch_set_launch")
+
+
 def shell_batch_state_layout(b: Batch):
     """(slots, row_offsets) of the packed state layout: resident slots in increasing order."""
     lib = load_library()

@@ -1600,6 +1600,15 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
   return SHELL_OK;
 }
 
+int shell_batch_set_launch(shell_batch *b, int32_t ctas_per_sm, int32_t share_x100, int32_t clusters) {
+  if (!b || ctas_per_sm < 1 || share_x100 < 1) return SHELL_ERR_INVALID_ARG;
+  b->occ = ctas_per_sm;
+  b->share_scale = share_x100 / 100.0;
+  b->policy = clusters ? 1 : 0;
+  b->dirty = true;
+  return SHELL_OK;
+}
+
 int shell_batch_set_profiling(shell_batch *b, int32_t on) {
   if (!b) return SHELL_ERR_INVALID_ARG;
   b->profiling = on != 0;
