@@ -39,7 +39,8 @@ EXPORTS = (
     "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
-    "shell_batch_autotune", "shell_batch_get_states", "shell_batch_set_states", "shell_batch_state_layout",
+    "shell_batch_autotune", "shell_batch_set_launch", "shell_batch_get_states", "shell_batch_set_states",
+    "shell_batch_state_layout",
     "shell_batch_destroy",
 )
 
@@ -131,6 +132,7 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_set_profiling": (C.c_int, [P, C.c_int32]),
         "shell_batch_kernel_times": (C.c_int, [P, P]),
         "shell_batch_autotune": (C.c_int, [P, C.c_int32, P, P]),
+        "shell_batch_set_launch": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
         "shell_batch_get_states": (C.c_int, [P, P, P]),
         "shell_batch_set_states": (C.c_int, [P, P, P]),
         "shell_batch_state_layout": (C.c_int, [P, P, P]),
