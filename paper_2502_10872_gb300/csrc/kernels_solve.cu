@@ -20,7 +20,8 @@
 //   gamma' = (r,u); delta' = (w,u); beta' = gamma'/gamma; alpha' = gamma'/(delta' - beta' gamma'/alpha).
 // FP64 mode: one CG in FP64 from the warm start v, until ||r|| <= rtol ||b||.
 // FP32 refinement mode: r64 = b - A v in FP64 (FP64 matrix and vector); inner CG in FP32 on A d = r64 from
-// d = 0 to a relative tolerance; v += d; repeat until ||r64|| <= refine_rtol ||b||.
+// d = 0 to a relative tolerance (or to a margin below the refinement target, if that is reached first);
+// v += d; repeat until ||r64|| <= refine_rtol ||b||.
 #include <algorithm>
 #include <cmath>
 
@@ -1096,8 +1097,11 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
         set_status(I, tm, SHELL_ERR_NOT_CONVERGED, total, rounds, rel);
         return true;
       }
+      // inner target: the relative reduction pcg_rtol, but no further than a margin below the refinement
+      // target (a round that starts close to it needs only a few iterations), and at least a halving
+      const double tol2 = fmin(fmax(tin2 * r2, 0.09 * tol_ref2), 0.25 * r2);
       double rho = 0.0;
-      const int it = cg_loop<float>(I, tm, reinterpret_cast<float *>(I.xs), tin2 * r2, I.pcg_max_it, &rho);
+      const int it = cg_loop<float>(I, tm, reinterpret_cast<float *>(I.xs), tol2, I.pcg_max_it, &rho);
       if (it == -2) return false;
       if (it == -3) {
         set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
