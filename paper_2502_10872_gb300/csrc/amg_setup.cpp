@@ -194,6 +194,53 @@ bool dense_inverse(const HostCsr &A, std::vector<double> &inv) {
   return true;
 }
 
+void csr_apply(const HostCsr &M, const std::vector<double> &x, std::vector<double> &y) {
+  y.assign(M.n, 0.0);
+  for (int i = 0; i < M.n; ++i) {
+    double s = 0.0;
+    for (int q = M.ptr[i]; q < M.ptr[i + 1]; ++q) s += M.val[q] * x[M.col[q]];
+    y[i] = s;
+  }
+}
+
+// y = V-cycle of levels >= l applied to b from a zero guess, with the steps of the GPU cycle: pre-smoothing
+// x = omega D^-1 b, residual, restriction, the coarser cycle, correction x += P y_c, post-smoothing
+// y = x + omega D^-1 (b - A x); the coarsest level is solved with its dense inverse or damped-Jacobi sweeps.
+void vcycle_host(const HostAmg &H, int l, const std::vector<double> &b, std::vector<double> &y) {
+  const HostAmgLevel &V = H.levels[l];
+  const int n = V.A.n;
+  std::vector<double> t;
+  if (l == (int)H.levels.size() - 1) {
+    if (H.coarse_sweeps == 0) {
+      y.assign(n, 0.0);
+      for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < n; ++j) s += H.coarse_inv[(size_t)i * n + j] * b[j];
+        y[i] = s;
+      }
+    } else {
+      y.resize(n);
+      for (int i = 0; i < n; ++i) y[i] = V.omega * V.dinv[i] * b[i];
+      for (int sw = 1; sw < H.coarse_sweeps; ++sw) {
+        csr_apply(V.A, y, t);
+        for (int i = 0; i < n; ++i) y[i] += V.omega * V.dinv[i] * (b[i] - t[i]);
+      }
+    }
+    return;
+  }
+  std::vector<double> x(n), r(n), bc, yc, px;
+  for (int i = 0; i < n; ++i) x[i] = V.omega * V.dinv[i] * b[i];
+  csr_apply(V.A, x, t);
+  for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
+  csr_apply(V.R, r, bc);
+  vcycle_host(H, l + 1, bc, yc);
+  csr_apply(V.P, yc, px);
+  for (int i = 0; i < n; ++i) x[i] += px[i];
+  csr_apply(V.A, x, t);
+  y.resize(n);
+  for (int i = 0; i < n; ++i) y[i] = x[i] + V.omega * V.dinv[i] * (b[i] - t[i]);
+}
+
 void finish_level(HostAmgLevel &L) {
   const int n = L.A.n;
   L.dinv.resize(n);
@@ -209,7 +256,7 @@ void finish_level(HostAmgLevel &L) {
 
 }  // namespace
 
-void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, double theta) {
+void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, double theta, int dense_max) {
   HostAmg &H = *out;
   H = HostAmg();
   H.levels.emplace_back();
@@ -268,6 +315,23 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
   } else {
     H.coarse_inv.clear();
     H.coarse_sweeps = 8;
+  }
+  // dense operator of the cycle below the first small level: column j = cycle applied to e_j
+  const int L = (int)H.levels.size();
+  for (int l = 1; l < L; ++l) {
+    const int n = H.levels[l].A.n;
+    if (n > dense_max) continue;
+    H.dense_level = l;
+    H.dense_n = n;
+    H.dense.assign((size_t)n * n, 0.0);
+    std::vector<double> e(n, 0.0), y;
+    for (int j = 0; j < n; ++j) {
+      e[j] = 1.0;
+      vcycle_host(H, l, e, y);
+      e[j] = 0.0;
+      for (int i = 0; i < n; ++i) H.dense[(size_t)j * n + i] = y[i];
+    }
+    break;
   }
 }
 

@@ -31,11 +31,18 @@ struct HostAmg {
   std::vector<HostAmgLevel> levels; // levels[L-1] is the coarsest
   std::vector<double> coarse_inv;   // dense inverse of the coarsest operator (row-major), empty if none
   int coarse_sweeps = 0;            // Jacobi sweeps on the coarsest level when it is too large to invert
+  // The V-cycle restricted to levels >= dense_level (started from zero) is a fixed linear map of that level's
+  // right-hand side: dense holds it as a dense n x n matrix, column-major (dense_level = -1: none).
+  int dense_level = -1;
+  int dense_n = 0;
+  std::vector<double> dense;
 };
 
 // Builds the hierarchy of the SPD matrix A (CSR, diagonal present). Rows whose only entry is the diagonal
 // (pinned vertices) are left out of the coarse spaces: the smoother solves them exactly.
-void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_max = 48, double theta = 0.08);
+// dense_max: the first level l >= 1 of at most dense_max rows gets the dense operator of the cycle below it.
+void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_max = 48, double theta = 0.08,
+               int dense_max = 400);
 
 HostSell to_sell(const HostCsr &M);
 

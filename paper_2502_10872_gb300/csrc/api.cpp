@@ -731,15 +731,18 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   build_amg(A, &H);
   const int L = (int)H.levels.size();
   if (L < 2) return SHELL_OK;
-  // one V(1,1) cycle reads every level operator twice, P and R once (8 B per FP32 nonzero with its
-  // column), about 200 B per row of level vectors, and the dense coarsest inverse once
+  // one V(1,1) cycle reads every level operator above the dense level twice, P and R once (8 B per FP32
+  // nonzero with its column), about 200 B per row of level vectors, and the dense operator (or the dense
+  // coarsest inverse) once
+  const int top = H.dense_level > 0 ? H.dense_level : L - 1;
   h->vcycle_bytes = 0;
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < top; ++l) {
     const HostAmgLevel &V = H.levels[l];
     h->vcycle_bytes += 16 * (int64_t)V.A.val.size() + 200 * (int64_t)V.A.n;
-    if (l < L - 1) h->vcycle_bytes += 8 * (int64_t)(V.P.val.size() + V.R.val.size());
+    h->vcycle_bytes += 8 * (int64_t)(V.P.val.size() + V.R.val.size());
   }
-  h->vcycle_bytes += 4 * (int64_t)H.coarse_inv.size();
+  h->vcycle_bytes += 200 * (int64_t)H.levels[top].A.n;
+  h->vcycle_bytes += 4 * (int64_t)(H.dense_level > 0 ? H.dense.size() : H.coarse_inv.size());
   std::vector<HostSell> As(L), Ps(L), Rs(L);
   for (int l = 0; l < L; ++l) {
     if (l > 0) As[l] = to_sell(H.levels[l].A);
@@ -761,8 +764,8 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   }
   const int nc = H.levels[L - 1].A.n;
   std::vector<AmgDev> lev(L);
-  double *cinv64 = nullptr;
-  float *cinv32 = nullptr;
+  double *cinv64 = nullptr, *dense64 = nullptr;
+  float *cinv32 = nullptr, *dense32 = nullptr;
   AmgDev *d_lev = nullptr;
   auto layout = [&](Carver &C) {
     for (int l = 0; l < L; ++l) {
@@ -811,6 +814,8 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
     }
     cinv64 = C.take<double>(H.coarse_inv.size());
     cinv32 = C.take<float>(H.coarse_inv.size());
+    dense64 = C.take<double>(H.dense.size());
+    dense32 = C.take<float>(H.dense.size());
     d_lev = C.take<AmgDev>(L);
   };
   Carver sz;
@@ -860,17 +865,16 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   }
   CK(up(cinv64, H.coarse_inv.data(), 8 * H.coarse_inv.size()));
   CK(up(cinv32, f32(H.coarse_inv), 4 * H.coarse_inv.size()));
+  CK(up(dense64, H.dense.data(), 8 * H.dense.size()));
+  CK(up(dense32, f32(H.dense), 4 * H.dense.size()));
   CK(up(d_lev, lev.data(), sizeof(AmgDev) * L));
   I.amg_levels = L;
   I.amg_coarse_n = nc;
   I.amg_coarse_sweeps = H.coarse_sweeps;
-  // agglomeration: the first level of at most one block of rows (classic phase structure without staging)
-  I.amg_agg = L;
-  for (int l = 1; stage && l < L; ++l)
-    if (H.levels[l].A.n <= kBlock) {
-      I.amg_agg = l;
-      break;
-    }
+  I.amg_dense_level = H.dense_level;
+  I.amg_dense_n = H.dense_n;
+  I.amg_dense64 = dense64;
+  I.amg_dense32 = dense32;
   I.amg = d_lev;
   I.amg_cinv64 = cinv64;
   I.amg_cinv32 = cinv32;

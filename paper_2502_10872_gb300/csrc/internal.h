@@ -151,10 +151,13 @@ struct Inst {
   int32_t amg_levels;
   int32_t amg_coarse_n;          // rows of the coarsest level
   int32_t amg_coarse_sweeps;     // 0: dense inverse on the coarsest level, else Jacobi sweeps
-  int32_t amg_agg;               // first level a multi-CTA team hands to its rank-0 CTA (amg_levels: none)
+  int32_t amg_dense_level;       // level whose cycle is applied as one dense operator (-1: none)
   AmgDev *amg;                   // [amg_levels]
   double *amg_cinv64;            // dense inverse of the coarsest operator [n][n]
   float *amg_cinv32;
+  int32_t amg_dense_n, pad2;     // rows of that level
+  double *amg_dense64;           // the cycle of levels >= amg_dense_level as a dense matrix, column-major
+  float *amg_dense32;
 };
 
 // A force tile: kForceBlock consecutive stencils of one instance.

@@ -591,6 +591,7 @@ struct LevelVal<float> {
   __device__ static const float *r(const AmgDev &L) { return L.r_val32; }
   __device__ static const float *dinv(const AmgDev &L) { return L.dinv32; }
   __device__ static const float *cinv(const Inst &I) { return I.amg_cinv32; }
+  __device__ static const float *dense(const Inst &I) { return I.amg_dense32; }
 };
 template <>
 struct LevelVal<double> {
@@ -599,6 +600,7 @@ struct LevelVal<double> {
   __device__ static const double *r(const AmgDev &L) { return L.r_val64; }
   __device__ static const double *dinv(const AmgDev &L) { return L.dinv64; }
   __device__ static const double *cinv(const Inst &I) { return I.amg_cinv64; }
+  __device__ static const double *dense(const Inst &I) { return I.amg_dense64; }
 };
 
 // plain y_i = sum_j m_ij v_j over a SELL-32 matrix (prolongation / restriction / FP64 level operators)
@@ -823,7 +825,9 @@ template <typename R>
 __device__ bool down_restrict(const Inst &I, int l, const Team &tm) {
   const AmgDev &A = I.amg[l];
   const AmgDev &C = I.amg[l + 1];
-  const bool pre = l + 1 < I.amg_levels - 1;   // the coarsest level is solved, not smoothed
+  // levels at and below the dense level, and the coarsest, are solved, not smoothed
+  const int top = I.amg_dense_level > 0 ? I.amg_dense_level : I.amg_levels - 1;
+  const bool pre = l + 1 < top;
   if (staged<R>(A.hr, tm.cap))
     lv_restrict<R, (sizeof(R) == 4)>(A, C, pre, tm);
   else
@@ -904,39 +908,76 @@ __device__ bool up_level(const Inst &I, int l, const Team &tm) {
   return team_sync(tm);
 }
 
-// u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing, Galerkin coarse operators and a dense
-// coarsest solve; output u in g (AoS). Expects vcycle_pre0 and a team barrier before it. The pre-smoothing
-// of each coarser level is fused into the restriction that produces its right-hand side.
-// Agglomeration: from level a = amg_agg on (at most one block of rows per level) a multi-CTA team hands the
-// cycle to its rank-0 CTA, which runs those phases alone with block barriers (the same products, so the
-// same values), while the other CTAs wait at one team barrier instead of one per phase. Returns false on
-// abort.
+// y_d = B b_d on the dense level d: B is the cycle of levels >= d (started from zero), a fixed linear map
+// set up on the host as a dense column-major matrix. This replaces that part of the cycle, a chain of
+// small dependent phases, by one product. Rows are split into contiguous chunks, one per CTA of the team;
+// inside a CTA, warp w sums the columns j = w, w + 8, ... in increasing order for 32 consecutive rows
+// (coalesced column reads of B), and the eight partial sums of a row are added in warp order: the same
+// operations whatever the team size.
+template <typename R>
+__device__ bool dense_level(const Inst &I, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  constexpr int U = 8;
+  const AmgDev &D = I.amg[I.amg_dense_level];
+  const G *b = reinterpret_cast<const G *>(D.b);
+  G *y = reinterpret_cast<G *>(D.y);
+  const R *B = LevelVal<R>::dense(I);
+  const int n = I.amg_dense_n;
+  const int per = (n + tm.size - 1) / tm.size;
+  const int r0 = tm.rank * per, r1 = min(n, r0 + per);
+  double(*part)[kBlock / 32][3] = stage_buf();   // [32 rows][8 warps][3], free between reductions
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = r0; base < r1; base += 32) {
+    const int i = base + lane;
+    R ax = R(0), ay = R(0), az = R(0);
+    if (i < r1) {
+      for (int j0 = w; j0 < n; j0 += 8 * U) {
+        R a[U];
+        G t[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = j0 + 8 * u;
+          a[u] = j < n ? B[(size_t)j * n + i] : R(0);
+          t[u] = ldg4(b + (j < n ? j : 0));
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          ax += a[u] * R(t[u].x);
+          ay += a[u] * R(t[u].y);
+          az += a[u] * R(t[u].z);
+        }
+      }
+    }
+    part[lane][w][0] = double(ax);
+    part[lane][w][1] = double(ay);
+    part[lane][w][2] = double(az);
+    __syncthreads();
+    if (w == 0 && i < r1) {
+      R sx = R(part[lane][0][0]), sy = R(part[lane][0][1]), sz = R(part[lane][0][2]);
+      for (int g = 1; g < kBlock / 32; ++g) {
+        sx += R(part[lane][g][0]);
+        sy += R(part[lane][g][1]);
+        sz += R(part[lane][g][2]);
+      }
+      y[i] = Vec<R>::mk(sx, sy, sz);
+    }
+    __syncthreads();
+  }
+  return team_sync(tm);
+}
+
+// u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing and Galerkin coarse operators; the part
+// of the cycle from the dense level down is one dense product (else the coarsest level is solved with its
+// dense inverse or Jacobi sweeps); output u in g (AoS). Expects vcycle_pre0 and a team barrier before it.
+// The pre-smoothing of each coarser level is fused into the restriction that produces its right-hand
+// side. Returns false on abort.
 template <typename R>
 __device__ bool vcycle(const Inst &I, const Team &tm) {
-  const int L = I.amg_levels;
-  const int a = (tm.size > 1 && I.amg_agg >= 1 && I.amg_agg < L) ? I.amg_agg : L;
-  for (int l = 0; l < a - 1; ++l)
+  const int top = I.amg_dense_level > 0 ? I.amg_dense_level : I.amg_levels - 1;
+  for (int l = 0; l < top; ++l)
     if (!down_resid<R>(I, l, tm) || !down_restrict<R>(I, l, tm)) return false;
-  if (a < L) {
-    if (!down_resid<R>(I, a - 1, tm)) return false;
-    if (tm.rank == 0) {
-      Team lt = tm;
-      lt.rank = 0;
-      lt.size = 1;
-      lt.mode = 0;
-      down_restrict<R>(I, a - 1, lt);
-      for (int l = a; l < L - 1; ++l) {
-        down_resid<R>(I, l, lt);
-        down_restrict<R>(I, l, lt);
-      }
-      coarsest<R>(I, lt);
-      for (int l = L - 2; l >= a; --l) up_level<R>(I, l, lt);
-    }
-    if (!team_sync(tm)) return false;
-  } else if (!coarsest<R>(I, tm)) {
-    return false;
-  }
-  for (int l = (a < L ? a - 1 : L - 2); l >= 0; --l)
+  if (!(I.amg_dense_level > 0 ? dense_level<R>(I, tm) : coarsest<R>(I, tm))) return false;
+  for (int l = top - 1; l >= 0; --l)
     if (!up_level<R>(I, l, tm)) return false;
   return true;
 }
