@@ -327,77 +327,78 @@ extern __shared__ float4 sh_halo[];   // dynamic shared memory: Team::cap entrie
 
 __device__ inline bool halo_on(const HaloDev &H, int cap) { return H.max > 0 && H.max <= cap; }
 
-// all threads of the CTA; vec is written by other CTAs of the launch, so it is read with coherent loads
-__device__ __forceinline__ void stage_halo(const HaloDev &H, int blk, const float4 *vec) {
+// One row of a staged product, all threads of the CTA (valid: this thread's row exists). The loads that do
+// not depend on the staged vector are issued before the staging barrier: the block's list bounds, the
+// row's slice bounds, its row sum and its first U nonzeros (column indices and values); so they overlap the
+// list -> vector -> shared-memory chain. vec is written by other CTAs of the launch, so it is read with
+// coherent loads. DIFF: difference form y_i = rs_i u_i + sum_j a_ij (u_j - u_i) of a square matrix (ui
+// returns u_i); else plain y_i = sum_j m_ij v_j. The arithmetic is that of the unstaged products.
+template <bool DIFF>
+__device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const float4 *vec, const int32_t *sp,
+                                           const float *__restrict__ val, const float *rs, int row, bool valid,
+                                           float &ax, float &ay, float &az, float4 &ui) {
+  constexpr int U = 8;
+  const int hb = H.ptr[blk], hn = H.ptr[blk + 1] - hb;
+  const int own = DIFF ? __ldg(H.own + blk) + (int)threadIdx.x : 0;
+  int p = 0, b1 = 0;
+  float r = 0.0f;
+  if (valid) {
+    const int s = row >> 5;
+    p = sp[s] + (row & 31);
+    b1 = sp[s + 1];
+    if (DIFF) r = rs[row];
+  }
+  int c[U];
+  float a[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = p + 32 * j;
+    const bool ok = q < b1;
+    c[j] = ok ? (int)H.c16[q] : own;
+    a[j] = ok ? val[q] : 0.0f;
+  }
   __syncthreads();   // earlier readers of the buffer are done
-  const int b = H.ptr[blk], n = H.ptr[blk + 1] - b;
   // two entries per thread and pass: both column loads, then both gathers, are in flight together
-  for (int k = threadIdx.x; k < n; k += 2 * kBlock) {
+  for (int k = threadIdx.x; k < hn; k += 2 * kBlock) {
     const int k2 = k + kBlock;
-    const int c0 = __ldg(H.col + b + k);
-    const int c1 = k2 < n ? __ldg(H.col + b + k2) : c0;
+    const int c0 = __ldg(H.col + hb + k);
+    const int c1 = k2 < hn ? __ldg(H.col + hb + k2) : c0;
     const float4 t0 = vec[c0];
     const float4 t1 = vec[c1];
     sh_halo[k] = t0;
-    if (k2 < n) sh_halo[k2] = t1;
+    if (k2 < hn) sh_halo[k2] = t1;
   }
   __syncthreads();
-}
-
-// difference form (square matrix) from the staged vector; own = local index of row
-__device__ inline void sell_diff_sh(const int32_t *sp, const uint16_t *c16, const float *__restrict__ val,
-                                    const float *rs, int own, int row, float &ax, float &ay, float &az) {
-  constexpr int U = 8;
-  const int s = row >> 5, lane = row & 31;
-  const int b1 = sp[s + 1];
-  const float4 ui = sh_halo[own];
-  const float r = rs[row];
-  ax = r * ui.x;
-  ay = r * ui.y;
-  az = r * ui.z;
-  for (int p = sp[s] + lane; p < b1; p += 32 * U) {
-    int c[U];
-    float a[U];
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int q = p + 32 * j;
-      const bool ok = q < b1;
-      c[j] = ok ? (int)c16[q] : own;
-      a[j] = ok ? val[q] : 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const float4 t = sh_halo[c[j]];
-      ax += a[j] * (t.x - ui.x);
-      ay += a[j] * (t.y - ui.y);
-      az += a[j] * (t.z - ui.z);
-    }
-  }
-}
-
-// plain y_i = sum_j m_ij v_j from the staged vector
-__device__ inline void sell_plain_sh(const int32_t *sp, const uint16_t *c16, const float *__restrict__ val, int row,
-                                     float &ax, float &ay, float &az) {
-  constexpr int U = 8;
-  const int s = row >> 5, lane = row & 31;
-  const int b1 = sp[s + 1];
   ax = ay = az = 0.0f;
-  for (int p = sp[s] + lane; p < b1; p += 32 * U) {
-    int c[U];
-    float a[U];
+  if (!valid) return;
+  if (DIFF) {
+    ui = sh_halo[own];
+    ax = r * ui.x;
+    ay = r * ui.y;
+    az = r * ui.z;
+  }
+  for (;;) {
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const float4 t = sh_halo[c[j]];
+      if (DIFF) {
+        ax += a[j] * (t.x - ui.x);
+        ay += a[j] * (t.y - ui.y);
+        az += a[j] * (t.z - ui.z);
+      } else {
+        ax += a[j] * t.x;
+        ay += a[j] * t.y;
+        az += a[j] * t.z;
+      }
+    }
+    p += 32 * U;
+    if (p >= b1) break;
 #pragma unroll
     for (int j = 0; j < U; ++j) {
       const int q = p + 32 * j;
       const bool ok = q < b1;
-      c[j] = ok ? (int)c16[q] : 0;
+      c[j] = ok ? (int)H.c16[q] : own;
       a[j] = ok ? val[q] : 0.0f;
-    }
-#pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const float4 t = sh_halo[c[j]];
-      ax += a[j] * t.x;
-      ay += a[j] * t.y;
-      az += a[j] * t.z;
     }
   }
 }
@@ -512,11 +513,8 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
       const int row = blk * kBlock + (int)threadIdx.x;
       if constexpr (sizeof(R) == 4) {
         if (st) {
-          stage_halo(I.h0, blk, g);
+          staged_row<true>(I.h0, blk, g, I.sl_ptr, val, I.rs32, row, row < nv, ax, ay, az, u);
           if (row >= nv) continue;
-          const int own = __ldg(I.h0.own + blk) + (int)threadIdx.x;
-          sell_diff_sh(I.sl_ptr, I.h0.c16, val, I.rs32, own, row, ax, ay, az);
-          u = sh_halo[own];
         } else {
           if (row >= nv) continue;
           spmv_row(I, val, g, row, ax, ay, az);
@@ -677,34 +675,6 @@ __device__ inline void level_a(const AmgDev &L, const D4 *v, int row, double &ax
   }
 // Row phases of one level, each instantiated with and without shared-memory staging (ST; FP32 only), so
 // that a launch's loop carries only the live values of the path it takes.
-template <bool ST, typename G>
-__device__ inline void stage_blk(const HaloDev &H, int blk, const G *vec) {
-  if constexpr (ST) stage_halo(H, blk, vec);
-}
-template <bool ST>
-__device__ inline void level_a_st(const AmgDev &L, const float4 *v, int blk, int row, float &ax, float &ay, float &az) {
-  if constexpr (ST)
-    sell_diff_sh(L.a_ptr, L.ha.c16, L.a_val32, L.rs32, __ldg(L.ha.own + blk) + (int)threadIdx.x, row, ax, ay, az);
-  else
-    level_a(L, v, row, ax, ay, az);
-}
-template <bool ST>
-__device__ inline void level_a_st(const AmgDev &L, const D4 *v, int, int row, double &ax, double &ay, double &az) {
-  level_a(L, v, row, ax, ay, az);
-}
-template <bool ST>
-__device__ inline void plain_st(const int32_t *sp, const int32_t *sc, const uint16_t *c16, const float *sv,
-                                const float4 *v, int row, float &ax, float &ay, float &az) {
-  if constexpr (ST)
-    sell_plain_sh(sp, c16, sv, row, ax, ay, az);
-  else
-    sell_plain<float, float4>(sp, sc, sv, v, row, ax, ay, az);
-}
-template <bool ST>
-__device__ inline void plain_st(const int32_t *sp, const int32_t *sc, const uint16_t *, const double *sv, const D4 *v,
-                                int row, double &ax, double &ay, double &az) {
-  sell_plain<double, D4>(sp, sc, sv, v, row, ax, ay, az);
-}
 
 // residual of level l: r = b - A x
 template <typename R, bool ST>
@@ -714,11 +684,16 @@ __device__ void lv_resid(const AmgDev &A, const Team &tm) {
   const G *x = reinterpret_cast<const G *>(A.x);
   G *rr = reinterpret_cast<G *>(A.r);
   for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
-    stage_blk<ST>(A.ha, ch, x);
     const int row = ch * kBlock + (int)threadIdx.x;
-    if (row >= A.n) continue;
     R ax, ay, az;
-    level_a_st<ST>(A, x, ch, row, ax, ay, az);
+    if constexpr (ST) {
+      float4 ui;
+      staged_row<true>(A.ha, ch, x, A.a_ptr, A.a_val32, A.rs32, row, row < A.n, ax, ay, az, ui);
+      if (row >= A.n) continue;
+    } else {
+      if (row >= A.n) continue;
+      level_a(A, x, row, ax, ay, az);
+    }
     const G bi = ldg4(b + row);
     rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
   }
@@ -734,11 +709,16 @@ __device__ void lv_restrict(const AmgDev &A, const AmgDev &C, bool pre, const Te
   const R *dinvc = LevelVal<R>::dinv(C);
   const R omc = R(C.omega);
   for (int ch = tm.rank; ch * kBlock < A.n_next; ch += tm.size) {
-    stage_blk<ST>(A.hr, ch, rr);
     const int row = ch * kBlock + (int)threadIdx.x;
-    if (row >= A.n_next) continue;
     R ax, ay, az;
-    plain_st<ST>(A.r_ptr, A.r_col, A.hr.c16, LevelVal<R>::r(A), rr, row, ax, ay, az);
+    if constexpr (ST) {
+      float4 unused;
+      staged_row<false>(A.hr, ch, rr, A.r_ptr, A.r_val32, nullptr, row, row < A.n_next, ax, ay, az, unused);
+      if (row >= A.n_next) continue;
+    } else {
+      if (row >= A.n_next) continue;
+      sell_plain<R, G>(A.r_ptr, A.r_col, LevelVal<R>::r(A), rr, row, ax, ay, az);
+    }
     bc[row] = Vec<R>::mk(ax, ay, az);
     if (pre) {
       const R d = omc * dinvc[row];
@@ -754,11 +734,16 @@ __device__ void lv_prolong(const AmgDev &A, const AmgDev &C, const Team &tm) {
   G *x = reinterpret_cast<G *>(A.x);
   const G *yc = reinterpret_cast<const G *>(C.y);
   for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
-    stage_blk<ST>(A.hp, ch, yc);
     const int row = ch * kBlock + (int)threadIdx.x;
-    if (row >= A.n) continue;
     R ax, ay, az;
-    plain_st<ST>(A.p_ptr, A.p_col, A.hp.c16, LevelVal<R>::p(A), yc, row, ax, ay, az);
+    if constexpr (ST) {
+      float4 unused;
+      staged_row<false>(A.hp, ch, yc, A.p_ptr, A.p_val32, nullptr, row, row < A.n, ax, ay, az, unused);
+      if (row >= A.n) continue;
+    } else {
+      if (row >= A.n) continue;
+      sell_plain<R, G>(A.p_ptr, A.p_col, LevelVal<R>::p(A), yc, row, ax, ay, az);
+    }
     const G xi = ldg4(x + row);
     x[row] = Vec<R>::mk(R(xi.x) + ax, R(xi.y) + ay, R(xi.z) + az);
   }
@@ -773,13 +758,18 @@ __device__ void lv_smooth(const AmgDev &A, typename Vec<R>::G *y, const Team &tm
   const R *dinv = LevelVal<R>::dinv(A);
   const R om = R(A.omega);
   for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
-    stage_blk<ST>(A.ha, ch, x);
     const int row = ch * kBlock + (int)threadIdx.x;
-    if (row >= A.n) continue;
     R ax, ay, az;
-    level_a_st<ST>(A, x, ch, row, ax, ay, az);
+    G xi;
+    if constexpr (ST) {
+      staged_row<true>(A.ha, ch, x, A.a_ptr, A.a_val32, A.rs32, row, row < A.n, ax, ay, az, xi);
+      if (row >= A.n) continue;
+    } else {
+      if (row >= A.n) continue;
+      level_a(A, x, row, ax, ay, az);
+      xi = ldg4(x + row);
+    }
     const G bi = ldg4(b + row);
-    const G xi = ldg4(x + row);
     const R d = om * dinv[row];
     y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
   }
