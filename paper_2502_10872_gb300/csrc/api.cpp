@@ -87,8 +87,7 @@ struct Carver {
 // gather lists of one matrix: device arrays carved from a block, then uploaded
 void halo_take(Carver &C, const HostHalo &H, HaloDev &D) {
   D = HaloDev{};
-  if (H.ptr.empty()) return;
-  D.ptr = C.take<int32_t>(H.ptr.size());
+  if (H.col.empty()) return;
   D.col = C.take<int32_t>(H.col.size());
   D.own = C.take<int32_t>(H.own.size());
   D.c16 = C.take<uint16_t>(H.c16.size());
@@ -96,9 +95,8 @@ void halo_take(Carver &C, const HostHalo &H, HaloDev &D) {
 }
 
 cudaError_t halo_upload(const HostHalo &H, const HaloDev &D, cudaStream_t st) {
-  if (H.ptr.empty()) return cudaSuccess;
+  if (H.col.empty()) return cudaSuccess;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(D.ptr, H.ptr.data(), 4 * H.ptr.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(D.col, H.col.data(), 4 * H.col.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(D.own, H.own.data(), 4 * H.own.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   return cudaMemcpyAsync(D.c16, H.c16.data(), 2 * H.c16.size(), cudaMemcpyHostToDevice, st);

@@ -11,7 +11,7 @@ bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, cons
   if (n_rows <= 0 || n_cols <= 0) return false;
   const int n_blocks = (n_rows + kHaloBlock - 1) / kHaloBlock;
   HostHalo H;
-  H.ptr.assign(n_blocks + 1, 0);
+  std::vector<std::vector<int32_t>> lists(n_blocks);
   H.own.assign(n_blocks, 0);
   H.c16.assign(sl_col.size(), 0);
   std::vector<int32_t> list;
@@ -45,9 +45,12 @@ bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, cons
         H.c16[pos] = (uint16_t)loc;
       }
     }
-    H.col.insert(H.col.end(), list.begin(), list.end());
-    H.ptr[b + 1] = (int32_t)H.col.size();
+    lists[b] = list;
   }
+  H.col.assign((size_t)n_blocks * H.max, 0);
+  for (int b = 0; b < n_blocks; ++b)
+    for (int k = 0; k < H.max; ++k)
+      H.col[(size_t)b * H.max + k] = k < (int)lists[b].size() ? lists[b][k] : lists[b][0];
   *out = std::move(H);
   return true;
 }

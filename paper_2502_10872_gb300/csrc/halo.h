@@ -3,7 +3,8 @@
 //
 // Block b is the 256 rows [256 b, 256 b + 256) that one CTA processes together. Its list holds, in
 // ascending order, every column that a stored (non-padding) entry of those rows references; for a square
-// matrix also each of its own rows. A product over the block first copies the vector entries of the list
+// matrix also each of its own rows. Lists are stored at a fixed stride (the longest list), padded with
+// their first entry, so a block's list starts at b * max without a lookup. A product over the block first copies the vector entries of the list
 // into shared memory, then reads every gathered value from there through a 16-bit local index per stored
 // entry. Padding entries get the local index of their own row (square) or 0 (value 0 either way).
 #pragma once
@@ -15,8 +16,7 @@ namespace shl {
 constexpr int kHaloBlock = 256;   // rows per block (the CTA size of the solve kernel)
 
 struct HostHalo {
-  std::vector<int32_t> ptr;       // [n_blocks + 1] offsets into col
-  std::vector<int32_t> col;       // concatenated lists
+  std::vector<int32_t> col;       // [n_blocks][max] lists, padded
   std::vector<int32_t> own;       // [n_blocks] local index of the block's first row (square matrices)
   std::vector<uint16_t> c16;      // [nnz_pad] local index of every stored entry
   int max = 0;                    // longest list

@@ -44,10 +44,11 @@ struct InstStatus {
 };
 
 // Per-block gather lists of a SELL-32 matrix (device pointers): block b = rows [256 b, 256 b + 256) stages the
-// vector entries col[ptr[b] .. ptr[b+1]) in shared memory; c16 is each stored entry's index into its block's
-// list; own[b] is the local index of the block's first row (square matrices). max = 0: no lists.
+// vector entries col[b * max .. b * max + max) in shared memory (lists padded to the longest, max); c16 is
+// each stored entry's index into its block's list; own[b] is the local index of the block's first row
+// (square matrices). max = 0: no lists.
 struct HaloDev {
-  int32_t *ptr, *col, *own;
+  int32_t *col, *own;
   uint16_t *c16;
   int32_t max, pad;
 };

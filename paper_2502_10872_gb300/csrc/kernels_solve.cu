@@ -328,17 +328,19 @@ extern __shared__ float4 sh_halo[];   // dynamic shared memory: Team::cap entrie
 __device__ inline bool halo_on(const HaloDev &H, int cap) { return H.max > 0 && H.max <= cap; }
 
 // One row of a staged product, all threads of the CTA (valid: this thread's row exists). The loads that do
-// not depend on the staged vector are issued before the staging barrier: the block's list bounds, the
-// row's slice bounds, its row sum and its first U nonzeros (column indices and values); so they overlap the
-// list -> vector -> shared-memory chain. vec is written by other CTAs of the launch, so it is read with
-// coherent loads. DIFF: difference form y_i = rs_i u_i + sum_j a_ij (u_j - u_i) of a square matrix (ui
-// returns u_i); else plain y_i = sum_j m_ij v_j. The arithmetic is that of the unstaged products.
+// not depend on the staged vector are issued before the staging barrier: the row's slice bounds, its row
+// sum and its first U nonzeros (column indices and values); so they overlap the list -> vector -> shared-
+// memory chain, which starts at once (lists sit at a fixed stride: no lookup of the block's list). vec is
+// written by other CTAs of the launch, so it is read with coherent loads. DIFF: difference form
+// y_i = rs_i u_i + sum_j a_ij (u_j - u_i) of a square matrix (ui returns u_i); else plain
+// y_i = sum_j m_ij v_j. The arithmetic is that of the unstaged products.
 template <bool DIFF>
 __device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const float4 *vec, const int32_t *sp,
                                            const float *__restrict__ val, const float *rs, int row, bool valid,
                                            float &ax, float &ay, float &az, float4 &ui) {
   constexpr int U = 8;
-  const int hb = H.ptr[blk], hn = H.ptr[blk + 1] - hb;
+  const int mx = H.max;
+  const int32_t *hl = H.col + (size_t)blk * mx;
   const int own = DIFF ? __ldg(H.own + blk) + (int)threadIdx.x : 0;
   int p = 0, b1 = 0;
   float r = 0.0f;
@@ -358,15 +360,21 @@ __device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const floa
     a[j] = ok ? val[q] : 0.0f;
   }
   __syncthreads();   // earlier readers of the buffer are done
-  // two entries per thread and pass: both column loads, then both gathers, are in flight together
-  for (int k = threadIdx.x; k < hn; k += 2 * kBlock) {
-    const int k2 = k + kBlock;
-    const int c0 = __ldg(H.col + hb + k);
-    const int c1 = k2 < hn ? __ldg(H.col + hb + k2) : c0;
+  // four entries per thread and pass: the column loads, then the gathers, are in flight together
+  for (int k = threadIdx.x; k < mx; k += 4 * kBlock) {
+    const bool o1 = k + kBlock < mx, o2 = k + 2 * kBlock < mx, o3 = k + 3 * kBlock < mx;
+    const int c0 = __ldg(hl + k);
+    const int c1 = o1 ? __ldg(hl + k + kBlock) : c0;
+    const int c2 = o2 ? __ldg(hl + k + 2 * kBlock) : c0;
+    const int c3 = o3 ? __ldg(hl + k + 3 * kBlock) : c0;
     const float4 t0 = vec[c0];
     const float4 t1 = vec[c1];
+    const float4 t2 = vec[c2];
+    const float4 t3 = vec[c3];
     sh_halo[k] = t0;
-    if (k2 < hn) sh_halo[k2] = t1;
+    if (o1) sh_halo[k + kBlock] = t1;
+    if (o2) sh_halo[k + 2 * kBlock] = t2;
+    if (o3) sh_halo[k + 3 * kBlock] = t3;
   }
   __syncthreads();
   ax = ay = az = 0.0f;
