@@ -335,6 +335,33 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
   }
 }
 
+HostSell to_sell4(const HostCsr &M) {
+  HostSell S;
+  S.n = M.n;
+  S.n_slices = (M.n + 7) / 8;
+  S.sl_ptr.assign(S.n_slices + 1, 0);
+  for (int s = 0; s < S.n_slices; ++s) {
+    int w = 0;
+    for (int i = 0; i < 8; ++i) {
+      const int r = s * 8 + i;
+      if (r < M.n) w = std::max(w, (M.ptr[r + 1] - M.ptr[r] + 3) / 4);
+    }
+    S.sl_ptr[s + 1] = S.sl_ptr[s] + 32 * w;
+  }
+  const int nnz = S.sl_ptr[S.n_slices];
+  S.sl_col.assign(nnz, 0);
+  S.val.assign(nnz, 0.0);
+  for (int r = 0; r < M.n; ++r) {
+    const int s = r / 8, i = r % 8;
+    for (int k = 0; k < M.ptr[r + 1] - M.ptr[r]; ++k) {
+      const int pos = S.sl_ptr[s] + 32 * (k / 4) + 4 * i + k % 4;
+      S.sl_col[pos] = M.col[M.ptr[r] + k];
+      S.val[pos] = M.val[M.ptr[r] + k];
+    }
+  }
+  return S;
+}
+
 HostSell to_sell(const HostCsr &M) {
   HostSell S;
   S.n = M.n;

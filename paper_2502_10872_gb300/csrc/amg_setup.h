@@ -46,4 +46,8 @@ void build_amg(const HostCsr &A, HostAmg *out, int max_levels = 12, int coarse_m
 
 HostSell to_sell(const HostCsr &M);
 
+// SELL with 4 lanes per row (for the long rows of the restriction): slices of 8 rows; entry k of the slice's
+// row i (i = 0..7) sits at sl_ptr[s] + 32 (k / 4) + 4 i + k % 4, padding column 0 with value 0.
+HostSell to_sell4(const HostCsr &M);
+
 }  // namespace shl

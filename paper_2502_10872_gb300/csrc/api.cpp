@@ -746,7 +746,7 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
     if (l > 0) As[l] = to_sell(H.levels[l].A);
     if (l < L - 1) {
       Ps[l] = to_sell(H.levels[l].P);
-      Rs[l] = to_sell(H.levels[l].R);
+      Rs[l] = to_sell4(H.levels[l].R);
     }
   }
   // gather lists for the FP32 products (level 0 shares the instance's)
@@ -757,7 +757,7 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
     if (l > 0) build_halo(V.A.n, V.A.n, As[l].sl_ptr, As[l].sl_col, V.A.ptr, true, &Ha[l]);
     if (l < L - 1) {
       build_halo(V.P.n, V.P.m, Ps[l].sl_ptr, Ps[l].sl_col, V.P.ptr, false, &Hp[l]);
-      build_halo(V.R.n, V.R.m, Rs[l].sl_ptr, Rs[l].sl_col, V.R.ptr, false, &Hr[l]);
+      build_halo(V.R.n, V.R.m, Rs[l].sl_ptr, Rs[l].sl_col, V.R.ptr, false, &Hr[l], 4);
     }
   }
   const int nc = H.levels[L - 1].A.n;

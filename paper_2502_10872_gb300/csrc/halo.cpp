@@ -1,4 +1,4 @@
-// halo.cpp -- per-block gather lists of a SELL-32 matrix (see halo.h).
+// halo.cpp -- per-block gather lists of a SELL matrix (see halo.h).
 #include "halo.h"
 
 #include <algorithm>
@@ -6,22 +6,27 @@
 namespace shl {
 
 bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, const std::vector<int32_t> &sl_col,
-                const std::vector<int32_t> &row_ptr, bool square, HostHalo *out) {
+                const std::vector<int32_t> &row_ptr, bool square, HostHalo *out, int lanes) {
   *out = HostHalo();
-  if (n_rows <= 0 || n_cols <= 0) return false;
-  const int n_blocks = (n_rows + kHaloBlock - 1) / kHaloBlock;
+  if (n_rows <= 0 || n_cols <= 0 || (lanes != 1 && lanes != 4)) return false;
+  const int rows_blk = kHaloBlock / lanes, rows_slice = 32 / lanes;
+  // position of entry k of row r in the SELL layout
+  auto pos_of = [&](int r, int k) {
+    const int s = r / rows_slice, i = r % rows_slice;
+    return sl_ptr[s] + 32 * (k / lanes) + lanes * i + k % lanes;
+  };
+  const int n_blocks = (n_rows + rows_blk - 1) / rows_blk;
   HostHalo H;
   std::vector<std::vector<int32_t>> lists(n_blocks);
   H.own.assign(n_blocks, 0);
   H.c16.assign(sl_col.size(), 0);
   std::vector<int32_t> list;
   for (int b = 0; b < n_blocks; ++b) {
-    const int r0 = b * kHaloBlock, r1 = std::min(n_rows, r0 + kHaloBlock);
+    const int r0 = b * rows_blk, r1 = std::min(n_rows, r0 + rows_blk);
     list.clear();
     for (int r = r0; r < r1; ++r) {
-      const int s = r / 32, l = r % 32;
       const int len = row_ptr[r + 1] - row_ptr[r];
-      for (int k = 0; k < len; ++k) list.push_back(sl_col[sl_ptr[s] + 32 * k + l]);
+      for (int k = 0; k < len; ++k) list.push_back(sl_col[pos_of(r, k)]);
       if (square) list.push_back(r);
     }
     if (list.empty()) list.push_back(0);
@@ -32,11 +37,11 @@ bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, cons
     const int own = square ? (int)(std::lower_bound(list.begin(), list.end(), r0) - list.begin()) : 0;
     H.own[b] = own;
     for (int r = r0; r < r1; ++r) {
-      const int s = r / 32, l = r % 32;
+      const int s = r / rows_slice;
       const int len = row_ptr[r + 1] - row_ptr[r];
-      const int w = (sl_ptr[s + 1] - sl_ptr[s]) / 32;
+      const int w = (sl_ptr[s + 1] - sl_ptr[s]) / 32 * lanes;   // stored entries of the row, padding included
       for (int k = 0; k < w; ++k) {
-        const int pos = sl_ptr[s] + 32 * k + l;
+        const int pos = pos_of(r, k);
         int loc;
         if (k < len)
           loc = (int)(std::lower_bound(list.begin(), list.end(), sl_col[pos]) - list.begin());

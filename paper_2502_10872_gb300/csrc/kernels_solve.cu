@@ -327,38 +327,11 @@ extern __shared__ float4 sh_halo[];   // dynamic shared memory: Team::cap entrie
 
 __device__ inline bool halo_on(const HaloDev &H, int cap) { return H.max > 0 && H.max <= cap; }
 
-// One row of a staged product, all threads of the CTA (valid: this thread's row exists). The loads that do
-// not depend on the staged vector are issued before the staging barrier: the row's slice bounds, its row
-// sum and its first U nonzeros (column indices and values); so they overlap the list -> vector -> shared-
-// memory chain, which starts at once (lists sit at a fixed stride: no lookup of the block's list). vec is
-// written by other CTAs of the launch, so it is read with coherent loads. DIFF: difference form
-// y_i = rs_i u_i + sum_j a_ij (u_j - u_i) of a square matrix (ui returns u_i); else plain
-// y_i = sum_j m_ij v_j. The arithmetic is that of the unstaged products.
-template <bool DIFF>
-__device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const float4 *vec, const int32_t *sp,
-                                           const float *__restrict__ val, const float *rs, int row, bool valid,
-                                           float &ax, float &ay, float &az, float4 &ui) {
-  constexpr int U = 8;
+// Copies block blk's list entries of vec into shared memory (all threads of the CTA; barriers on both sides).
+// vec is written by other CTAs of the launch, so it is read with coherent loads.
+__device__ __forceinline__ void stage_block(const HaloDev &H, int blk, const float4 *vec) {
   const int mx = H.max;
   const int32_t *hl = H.col + (size_t)blk * mx;
-  const int own = DIFF ? __ldg(H.own + blk) + (int)threadIdx.x : 0;
-  int p = 0, b1 = 0;
-  float r = 0.0f;
-  if (valid) {
-    const int s = row >> 5;
-    p = sp[s] + (row & 31);
-    b1 = sp[s + 1];
-    if (DIFF) r = rs[row];
-  }
-  int c[U];
-  float a[U];
-#pragma unroll
-  for (int j = 0; j < U; ++j) {
-    const int q = p + 32 * j;
-    const bool ok = q < b1;
-    c[j] = ok ? (int)H.c16[q] : own;
-    a[j] = ok ? val[q] : 0.0f;
-  }
   __syncthreads();   // earlier readers of the buffer are done
   // four entries per thread and pass: the column loads, then the gathers, are in flight together
   for (int k = threadIdx.x; k < mx; k += 4 * kBlock) {
@@ -377,6 +350,39 @@ __device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const floa
     if (o3) sh_halo[k + 3 * kBlock] = t3;
   }
   __syncthreads();
+}
+
+// One row of a staged product, all threads of the CTA (valid: this thread's row exists). The loads that do
+// not depend on the staged vector are issued before the staging barrier: the row's slice bounds, its row
+// sum and its first U nonzeros (column indices and values); so they overlap the list -> vector -> shared-
+// memory chain, which starts at once (lists sit at a fixed stride: no lookup of the block's list). vec is
+// written by other CTAs of the launch, so it is read with coherent loads. DIFF: difference form
+// y_i = rs_i u_i + sum_j a_ij (u_j - u_i) of a square matrix (ui returns u_i); else plain
+// y_i = sum_j m_ij v_j. The arithmetic is that of the unstaged products.
+template <bool DIFF>
+__device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const float4 *vec, const int32_t *sp,
+                                           const float *__restrict__ val, const float *rs, int row, bool valid,
+                                           float &ax, float &ay, float &az, float4 &ui) {
+  constexpr int U = 8;
+  const int own = DIFF ? __ldg(H.own + blk) + (int)threadIdx.x : 0;
+  int p = 0, b1 = 0;
+  float r = 0.0f;
+  if (valid) {
+    const int s = row >> 5;
+    p = sp[s] + (row & 31);
+    b1 = sp[s + 1];
+    if (DIFF) r = rs[row];
+  }
+  int c[U];
+  float a[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = p + 32 * j;
+    const bool ok = q < b1;
+    c[j] = ok ? (int)H.c16[q] : own;
+    a[j] = ok ? val[q] : 0.0f;
+  }
+  stage_block(H, blk, vec);
   ax = ay = az = 0.0f;
   if (!valid) return;
   if (DIFF) {
@@ -707,30 +713,80 @@ __device__ void lv_resid(const AmgDev &A, const Team &tm) {
   }
 }
 
-// restriction to level l+1 with its pre-smoothing from zero fused: bc = R r; xc = omega_c Dc^-1 bc
+// restriction to level l+1 with its pre-smoothing from zero fused: bc = R r; xc = omega_c Dc^-1 bc.
+// R has 4 lanes per row (its rows are long): a CTA takes 64 coarse rows, lane k % 4 of a row sums the
+// entries k, k + 4, ... in increasing order, and the four partial sums are added in a fixed shuffle tree;
+// staged (FP32) and unstaged products run the same arithmetic. The loads that do not depend on the staged
+// vector (slice bounds, first nonzeros) are issued before the staging barrier.
 template <typename R, bool ST>
 __device__ void lv_restrict(const AmgDev &A, const AmgDev &C, bool pre, const Team &tm) {
   typedef typename Vec<R>::G G;
+  constexpr int U = 8;
+  constexpr int kRows = kBlock / 4;   // coarse rows per CTA pass
   const G *rr = reinterpret_cast<const G *>(A.r);
   G *bc = reinterpret_cast<G *>(C.b);
   G *xc = reinterpret_cast<G *>(C.x);
   const R *dinvc = LevelVal<R>::dinv(C);
+  const R *val = LevelVal<R>::r(A);
   const R omc = R(C.omega);
-  for (int ch = tm.rank; ch * kBlock < A.n_next; ch += tm.size) {
-    const int row = ch * kBlock + (int)threadIdx.x;
-    R ax, ay, az;
-    if constexpr (ST) {
-      float4 unused;
-      staged_row<false>(A.hr, ch, rr, A.r_ptr, A.r_val32, nullptr, row, row < A.n_next, ax, ay, az, unused);
-      if (row >= A.n_next) continue;
-    } else {
-      if (row >= A.n_next) continue;
-      sell_plain<R, G>(A.r_ptr, A.r_col, LevelVal<R>::r(A), rr, row, ax, ay, az);
+  const int n = A.n_next;
+  const int lane = threadIdx.x & 31;
+  for (int ch = tm.rank; ch * kRows < n; ch += tm.size) {
+    const int row = ch * kRows + (int)(threadIdx.x >> 2);
+    const bool valid = row < n;
+    int p = 0, b1 = 0;
+    if (valid) {
+      const int s = row >> 3;
+      p = A.r_ptr[s] + lane;
+      b1 = A.r_ptr[s + 1];
     }
-    bc[row] = Vec<R>::mk(ax, ay, az);
-    if (pre) {
-      const R d = omc * dinvc[row];
-      xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
+    int c[U];
+    R a[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
+      a[j] = ok ? val[q] : R(0);
+    }
+    if constexpr (ST) stage_block(A.hr, ch, reinterpret_cast<const float4 *>(rr));
+    R ax = R(0), ay = R(0), az = R(0);
+    if (valid) {
+      for (;;) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          G t;
+          if constexpr (ST)
+            t = sh_halo[c[j]];
+          else
+            t = ldg4(rr + c[j]);
+          ax += a[j] * R(t.x);
+          ay += a[j] * R(t.y);
+          az += a[j] * R(t.z);
+        }
+        p += 32 * U;
+        if (p >= b1) break;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const int q = p + 32 * j;
+          const bool ok = q < b1;
+          c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
+          a[j] = ok ? val[q] : R(0);
+        }
+      }
+    }
+    ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+    ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+    az += __shfl_xor_sync(0xffffffffu, az, 1);
+    ax += __shfl_xor_sync(0xffffffffu, ax, 2);
+    ay += __shfl_xor_sync(0xffffffffu, ay, 2);
+    az += __shfl_xor_sync(0xffffffffu, az, 2);
+    if (valid && (threadIdx.x & 3) == 0) {
+      bc[row] = Vec<R>::mk(ax, ay, az);
+      if (pre) {
+        const R d = omc * dinvc[row];
+        xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
+      }
     }
   }
 }
