@@ -743,7 +743,7 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   h->vcycle_bytes += 4 * (int64_t)(H.dense_level > 0 ? H.dense.size() : H.coarse_inv.size());
   std::vector<HostSell> As(L), Ps(L), Rs(L);
   for (int l = 0; l < L; ++l) {
-    if (l > 0) As[l] = to_sell(H.levels[l].A);
+    if (l > 0) As[l] = to_sell4(H.levels[l].A);
     if (l < L - 1) {
       Ps[l] = to_sell(H.levels[l].P);
       Rs[l] = to_sell4(H.levels[l].R);
@@ -754,7 +754,7 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   std::vector<HostHalo> Ha(L), Hp(L), Hr(L);
   for (int l = 0; stage32 && l < L; ++l) {
     const HostAmgLevel &V = H.levels[l];
-    if (l > 0) build_halo(V.A.n, V.A.n, As[l].sl_ptr, As[l].sl_col, V.A.ptr, true, &Ha[l]);
+    if (l > 0) build_halo(V.A.n, V.A.n, As[l].sl_ptr, As[l].sl_col, V.A.ptr, true, &Ha[l], 4);
     if (l < L - 1) {
       build_halo(V.P.n, V.P.m, Ps[l].sl_ptr, Ps[l].sl_col, V.P.ptr, false, &Hp[l]);
       build_halo(V.R.n, V.R.m, Rs[l].sl_ptr, Rs[l].sl_col, V.R.ptr, false, &Hr[l], 4);

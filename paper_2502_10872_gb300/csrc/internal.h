@@ -53,10 +53,11 @@ struct HaloDev {
   int32_t max, pad;
 };
 
-// One level of the smoothed-aggregation multigrid preconditioner (device pointers). A (this level's
-// operator) and P (rows of this level -> columns of the next) are SELL-32; R = P^T (rows of the next level
-// -> columns of this one), whose rows are long, is SELL with 4 lanes per row (slices of 8 rows, entry k of
-// slice row i at r_ptr[s] + 32 (k / 4) + 4 i + k % 4) and its gather lists cover 64-row blocks. Level vectors are array-of-structures [n][4] in the solve precision.
+// One level of the smoothed-aggregation multigrid preconditioner (device pointers). P (rows of this level ->
+// columns of the next) and the level-0 operator are SELL-32; R = P^T (rows of the next level -> columns of
+// this one) and the coarse operators A (levels >= 1), whose rows are long, are SELL with 4 lanes per row
+// (slices of 8 rows, entry k of slice row i at ptr[s] + 32 (k / 4) + 4 i + k % 4), with gather lists over
+// 64-row blocks. Level vectors are array-of-structures [n][4] in the solve precision.
 struct AmgDev {
   int32_t n, n_next;
   int32_t *a_ptr, *a_col;

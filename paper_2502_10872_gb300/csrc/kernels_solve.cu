@@ -839,6 +839,133 @@ __device__ void lv_smooth(const AmgDev &A, typename Vec<R>::G *y, const Team &tm
   }
 }
 
+// ---- coarse levels (l >= 1): A stored with 4 lanes per row (8-row slices, like R), 64-row CTA passes.
+// One row of A x for the pass over block blk: lane k % 4 sums the entries k, k + 4, ... in increasing order,
+// the four partial sums are added in a fixed shuffle tree; FP32 in difference form
+// (A x)_i = rs_i x_i + sum_j a_ij (x_j - x_i), FP64 plain. Staged (ST, FP32) and unstaged products, and
+// any team size, run the same arithmetic. All 4 lanes of a row return the row's value; ui = x_i.
+template <typename R, bool ST>
+__device__ __forceinline__ void coarse_row(const AmgDev &A, const typename Vec<R>::G *x, int blk, int row,
+                                           bool valid, R &ax, R &ay, R &az, typename Vec<R>::G &ui) {
+  typedef typename Vec<R>::G G;
+  constexpr int U = 8;
+  constexpr bool DIFF = sizeof(R) == 4;
+  const R *val = LevelVal<R>::a(A);
+  const int lane = threadIdx.x & 31;
+  const int own = ST ? __ldg(A.ha.own + blk) + (int)(threadIdx.x >> 2) : row;
+  int p = 0, b1 = 0;
+  R r = R(0);
+  if (valid) {
+    const int s = row >> 3;
+    p = A.a_ptr[s] + lane;
+    b1 = A.a_ptr[s + 1];
+    if constexpr (DIFF) r = A.rs32[row];
+  }
+  int c[U];
+  R a[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = p + 32 * j;
+    const bool ok = q < b1;
+    c[j] = ok ? (ST ? (int)A.ha.c16[q] : A.a_col[q]) : own;
+    a[j] = ok ? val[q] : R(0);
+  }
+  if constexpr (ST) stage_block(A.ha, blk, reinterpret_cast<const float4 *>(x));
+  R px = R(0), py = R(0), pz = R(0);
+  ui = G{};
+  if (valid) {
+    if constexpr (ST)
+      ui = sh_halo[own];
+    else
+      ui = ldg4(x + row);
+    for (;;) {
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        G t;
+        if constexpr (ST)
+          t = sh_halo[c[j]];
+        else
+          t = ldg4(x + c[j]);
+        if constexpr (DIFF) {
+          px += a[j] * (R(t.x) - R(ui.x));
+          py += a[j] * (R(t.y) - R(ui.y));
+          pz += a[j] * (R(t.z) - R(ui.z));
+        } else {
+          px += a[j] * R(t.x);
+          py += a[j] * R(t.y);
+          pz += a[j] * R(t.z);
+        }
+      }
+      p += 32 * U;
+      if (p >= b1) break;
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int q = p + 32 * j;
+        const bool ok = q < b1;
+        c[j] = ok ? (ST ? (int)A.ha.c16[q] : A.a_col[q]) : own;
+        a[j] = ok ? val[q] : R(0);
+      }
+    }
+  }
+  px += __shfl_xor_sync(0xffffffffu, px, 1);
+  py += __shfl_xor_sync(0xffffffffu, py, 1);
+  pz += __shfl_xor_sync(0xffffffffu, pz, 1);
+  px += __shfl_xor_sync(0xffffffffu, px, 2);
+  py += __shfl_xor_sync(0xffffffffu, py, 2);
+  pz += __shfl_xor_sync(0xffffffffu, pz, 2);
+  if constexpr (DIFF) {
+    ax = r * R(ui.x) + px;
+    ay = r * R(ui.y) + py;
+    az = r * R(ui.z) + pz;
+  } else {
+    ax = px;
+    ay = py;
+    az = pz;
+  }
+}
+
+// residual of a coarse level: r = b - A x
+template <typename R, bool ST>
+__device__ void lv_resid4(const AmgDev &A, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const G *b = reinterpret_cast<const G *>(A.b);
+  const G *x = reinterpret_cast<const G *>(A.x);
+  G *rr = reinterpret_cast<G *>(A.r);
+  for (int ch = tm.rank; ch * (kBlock / 4) < A.n; ch += tm.size) {
+    const int row = ch * (kBlock / 4) + (int)(threadIdx.x >> 2);
+    const bool valid = row < A.n;
+    R ax, ay, az;
+    G ui;
+    coarse_row<R, ST>(A, x, ch, row, valid, ax, ay, az, ui);
+    if (valid && (threadIdx.x & 3) == 0) {
+      const G bi = ldg4(b + row);
+      rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
+    }
+  }
+}
+
+// damped-Jacobi sweep of a coarse level: y = x + omega D^-1 (b - A x) (post-smoothing: x is the corrected
+// pre-smoothed vector; coarsest-level sweeps: x the previous sweep)
+template <typename R, bool ST>
+__device__ void lv_smooth4(const AmgDev &A, const typename Vec<R>::G *x, typename Vec<R>::G *y, const Team &tm) {
+  typedef typename Vec<R>::G G;
+  const G *b = reinterpret_cast<const G *>(A.b);
+  const R *dinv = LevelVal<R>::dinv(A);
+  const R om = R(A.omega);
+  for (int ch = tm.rank; ch * (kBlock / 4) < A.n; ch += tm.size) {
+    const int row = ch * (kBlock / 4) + (int)(threadIdx.x >> 2);
+    const bool valid = row < A.n;
+    R ax, ay, az;
+    G xi;
+    coarse_row<R, ST>(A, x, ch, row, valid, ax, ay, az, xi);
+    if (valid && (threadIdx.x & 3) == 0) {
+      const G bi = ldg4(b + row);
+      const R d = om * dinv[row];
+      y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+    }
+  }
+}
+
 // staging applies to FP32 products whose lists fit the launch's buffer
 template <typename R>
 __device__ inline bool staged(const HaloDev &H, int cap) {
@@ -869,10 +996,18 @@ __device__ void vcycle_pre0(const Inst &I, const Team &tm) {
 template <typename R>
 __device__ bool down_resid(const Inst &I, int l, const Team &tm) {
   const AmgDev &A = I.amg[l];
-  if (staged<R>(A.ha, tm.cap))
-    lv_resid<R, (sizeof(R) == 4)>(A, tm);
-  else
-    lv_resid<R, false>(A, tm);
+  const bool st = staged<R>(A.ha, tm.cap);
+  if (l == 0) {
+    if (st)
+      lv_resid<R, (sizeof(R) == 4)>(A, tm);
+    else
+      lv_resid<R, false>(A, tm);
+  } else {
+    if (st)
+      lv_resid4<R, (sizeof(R) == 4)>(A, tm);
+    else
+      lv_resid4<R, false>(A, tm);
+  }
   return team_sync(tm);
 }
 template <typename R>
@@ -924,14 +1059,7 @@ __device__ bool coarsest(const Inst &I, const Team &tm) {
   for (int sw = 1; sw < I.amg_coarse_sweeps; ++sw) {
     G *src = (sw & 1) ? y : x;
     G *dst = (sw & 1) ? x : y;
-    LEVEL_ROWS_BEGIN(C.n, tm)
-    R ax, ay, az;
-    level_a(C, src, row, ax, ay, az);
-    const G bi = ldg4(b + row);
-    const G xi = ldg4(src + row);
-    const R d = om * dinv[row];
-    dst[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
-    LEVEL_ROWS_END
+    lv_smooth4<R, false>(C, src, dst, tm);
     if (!team_sync(tm)) return false;
   }
   if ((I.amg_coarse_sweeps & 1) == 0) {   // the last sweep wrote x: move it to y
@@ -955,10 +1083,19 @@ __device__ bool up_level(const Inst &I, int l, const Team &tm) {
   else
     lv_prolong<R, false>(A, C, tm);
   if (!team_sync(tm)) return false;
-  if (staged<R>(A.ha, tm.cap))
-    lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
-  else
-    lv_smooth<R, false>(A, y, tm);
+  const bool st = staged<R>(A.ha, tm.cap);
+  const G *x = reinterpret_cast<const G *>(A.x);
+  if (l == 0) {
+    if (st)
+      lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
+    else
+      lv_smooth<R, false>(A, y, tm);
+  } else {
+    if (st)
+      lv_smooth4<R, (sizeof(R) == 4)>(A, x, y, tm);
+    else
+      lv_smooth4<R, false>(A, x, y, tm);
+  }
   return team_sync(tm);
 }
 
