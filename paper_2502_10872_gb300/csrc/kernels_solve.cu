@@ -468,9 +468,14 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
 
 // FP64 residual r64 = b - A64 sol; returns partial ||r64||^2. If R is float also prepares the inner CG:
 // r32 = r64, xs = 0, g32 = D32^-1 r32. If R is double: r = r64 (in place), sol unchanged, g = D^-1 r.
+// Multigrid: also the first V-cycle's level-0 pre-smoothing from zero, b0 = r, x0 = omega D^-1 r (row-local).
 template <typename R>
 __device__ void phase_resid(const Inst &I, const Team &tm) {
   const int nv = I.nv;
+  const bool amg = I.amg_levels > 0;
+  typename Vec<R>::G *b0 = amg ? reinterpret_cast<typename Vec<R>::G *>(I.amg[0].b) : nullptr;
+  typename Vec<R>::G *x0 = amg ? reinterpret_cast<typename Vec<R>::G *>(I.amg[0].x) : nullptr;
+  const R om0 = amg ? R(I.amg[0].omega) : R(0);
   const D4 *g64 = reinterpret_cast<const D4 *>(I.g64);
   R *r = reinterpret_cast<R *>(I.r);
   R *xs = reinterpret_cast<R *>(I.xs);
@@ -500,6 +505,11 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
       }
       const R di = dinv[row];
       g[row] = Vec<R>::mk(di * q0, di * q1, di * q2);
+      if (amg) {
+        b0[row] = Vec<R>::mk(q0, q1, q2);
+        const R d = om0 * di;
+        x0[row] = Vec<R>::mk(d * q0, d * q1, d * q2);
+      }
     }
     stage_chunk<double>(cs, I, tm, ch, rr2, 0.0, 0.0);
   }
@@ -564,6 +574,11 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
   R *p = reinterpret_cast<R *>(I.p);
   R *s = reinterpret_cast<R *>(I.s);
   const R *w = reinterpret_cast<const R *>(I.w);
+  // multigrid: the level-0 pre-smoothing from zero (b0 = r, x0 = omega D^-1 r) of the next V-cycle is
+  // row-local, so it is done here from the new r
+  typename Vec<R>::G *b0 = amg ? reinterpret_cast<typename Vec<R>::G *>(I.amg[0].b) : nullptr;
+  typename Vec<R>::G *x0 = amg ? reinterpret_cast<typename Vec<R>::G *>(I.amg[0].x) : nullptr;
+  const R om0 = amg ? R(I.amg[0].omega) : R(0);
   ROWS_BEGIN(I, tm)
   const R di = dinv[row];
   R uo[3];
@@ -573,7 +588,7 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
     uo[1] = R(gu.y);
     uo[2] = R(gu.z);
   }
-  R un[3];
+  R rv[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
@@ -586,9 +601,15 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
     x[k] += alpha * pc;
     const R rn = rc - alpha * sc;
     r[k] = rn;
-    un[c] = di * rn;
+    rv[c] = rn;
   }
-  if (!amg) g[row] = Vec<R>::mk(un[0], un[1], un[2]);
+  if (!amg) {
+    g[row] = Vec<R>::mk(di * rv[0], di * rv[1], di * rv[2]);
+  } else {
+    b0[row] = Vec<R>::mk(rv[0], rv[1], rv[2]);
+    const R d = om0 * di;
+    x0[row] = Vec<R>::mk(d * rv[0], d * rv[1], d * rv[2]);
+  }
   ROWS_END
 }
 
@@ -972,26 +993,6 @@ __device__ inline bool staged(const HaloDev &H, int cap) {
   return sizeof(R) == 4 && halo_on(H, cap);
 }
 
-// Pre-smoothing of level 0 from zero, row-local: b0 = r, x0 = omega D0^-1 r. It runs right after the phase
-// that wrote r for these rows (same thread), so it needs no barrier of its own.
-template <typename R>
-__device__ void vcycle_pre0(const Inst &I, const Team &tm) {
-  typedef typename Vec<R>::G G;
-  const AmgDev &A = I.amg[0];
-  const R *rin = reinterpret_cast<const R *>(I.r);
-  const int nv = I.nv;
-  G *b = reinterpret_cast<G *>(A.b);
-  G *x = reinterpret_cast<G *>(A.x);
-  const R *dinv = LevelVal<R>::dinv(A);
-  const R om = R(A.omega);
-  LEVEL_ROWS_BEGIN(A.n, tm)
-  const R r0 = rin[row], r1 = rin[nv + row], r2 = rin[2 * nv + row];
-  b[row] = Vec<R>::mk(r0, r1, r2);
-  const R d = om * dinv[row];
-  x[row] = Vec<R>::mk(d * r0, d * r1, d * r2);
-  LEVEL_ROWS_END
-}
-
 // One level of the down sweep: residual, then restriction (with the next level's pre-smoothing fused).
 template <typename R>
 __device__ bool down_resid(const Inst &I, int l, const Team &tm) {
@@ -1159,7 +1160,8 @@ __device__ bool dense_level(const Inst &I, const Team &tm) {
 
 // u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing and Galerkin coarse operators; the part
 // of the cycle from the dense level down is one dense product (else the coarsest level is solved with its
-// dense inverse or Jacobi sweeps); output u in g (AoS). Expects vcycle_pre0 and a team barrier before it.
+// dense inverse or Jacobi sweeps); output u in g (AoS). Expects the level-0 pre-smoothing (done by the
+// phase that wrote r) and a team barrier before it.
 // The pre-smoothing of each coarser level is fused into the restriction that produces its right-hand
 // side. Returns false on abort.
 template <typename R>
@@ -1178,7 +1180,6 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
 // -3 on a non-finite reduction.
 template <typename R>
 __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, double *rho_out) {
-  if (I.amg_levels > 0) vcycle_pre0<R>(I, tm);
   if (!team_sync(tm)) return -2;
   if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
   phase_spmv<R>(I, tm);
@@ -1193,7 +1194,6 @@ __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, d
   bool first = true;
   for (int it = 1; it <= max_it; ++it) {
     phase_update<R>(I, tm, R(alpha), R(beta), first, x);
-    if (I.amg_levels > 0) vcycle_pre0<R>(I, tm);
     if (!team_sync(tm)) return -2;
     if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
     phase_spmv<R>(I, tm);
