@@ -417,6 +417,64 @@ __device__ __forceinline__ void staged_row(const HaloDev &H, int blk, const floa
   }
 }
 
+// FP64 plain product of the level matrix from staged FP64 entries (the refinement residual of FP32
+// instances, which carry the matrix's gather lists): the buffer holds D4 entries (two float4 slots each);
+// the loads that do not depend on the staged vector go first; the arithmetic is that of spmv_row (FP64).
+__device__ __forceinline__ void staged_row64(const HaloDev &H, int blk, const D4 *vec, const int32_t *sp,
+                                             const double *__restrict__ val, int row, bool valid, double &ax,
+                                             double &ay, double &az) {
+  constexpr int U = 4;
+  D4 *sh = reinterpret_cast<D4 *>(sh_halo);
+  int p = 0, b1 = 0;
+  if (valid) {
+    const int s = row >> 5;
+    p = sp[s] + (row & 31);
+    b1 = sp[s + 1];
+  }
+  int c[U];
+  double a[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int q = p + 32 * j;
+    const bool ok = q < b1;
+    c[j] = ok ? (int)H.c16[q] : 0;
+    a[j] = ok ? val[q] : 0.0;
+  }
+  const int mx = H.max;
+  const int32_t *hl = H.col + (size_t)blk * mx;
+  __syncthreads();   // earlier readers of the buffer are done
+  for (int k = threadIdx.x; k < mx; k += 2 * kBlock) {
+    const bool o1 = k + kBlock < mx;
+    const int c0 = __ldg(hl + k);
+    const int c1 = o1 ? __ldg(hl + k + kBlock) : c0;
+    const D4 t0 = ldg4(vec + c0);
+    const D4 t1 = ldg4(vec + c1);
+    sh[k] = t0;
+    if (o1) sh[k + kBlock] = t1;
+  }
+  __syncthreads();
+  ax = ay = az = 0.0;
+  if (!valid) return;
+  for (;;) {
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const D4 t = sh[c[j]];
+      ax += a[j] * t.x;
+      ay += a[j] * t.y;
+      az += a[j] * t.z;
+    }
+    p += 32 * U;
+    if (p >= b1) break;
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+      const int q = p + 32 * j;
+      const bool ok = q < b1;
+      c[j] = ok ? (int)H.c16[q] : 0;
+      a[j] = ok ? val[q] : 0.0;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ phases
 #define ROWS_BEGIN(I, tm)                                                                 \
   for (int ch = (tm).rank; ch < (I).n_chunks; ch += (tm).size) {                        \
@@ -481,14 +539,22 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
   R *xs = reinterpret_cast<R *>(I.xs);
   typename Vec<R>::G *g = Vec<R>::g(I);
   const R *dinv = Vec<R>::dinv(I);
+  const bool st = I.h0.max > 0 && 2 * I.h0.max <= tm.cap;   // FP64 entries take two buffer slots
   ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
     double rr2 = 0.0;
     for (int rr = 0; rr < I.rows_per_thread; ++rr) {
-      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
-      if (row >= nv) continue;
+      const int blk = ch * I.rows_per_thread + rr;
+      if (blk * kBlock >= nv) break;
+      const int row = blk * kBlock + (int)threadIdx.x;
       double ax, ay, az;
-      spmv_row(I, I.val64, g64, row, ax, ay, az);
+      if (st) {
+        staged_row64(I.h0, blk, g64, I.sl_ptr, I.val64, row, row < nv, ax, ay, az);
+        if (row >= nv) continue;
+      } else {
+        if (row >= nv) continue;
+        spmv_row(I, I.val64, g64, row, ax, ay, az);
+      }
       const double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
       I.r64[row] = r0;
       I.r64[nv + row] = r1;
