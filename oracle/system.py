@@ -230,3 +230,51 @@ def step(m: Model, x, v, n_steps=1):
         v = m._lu.solve(rhs(m, x, v))
         x = x + m.dt * v
     return x, v
+
+
+# ------------------------------------------------------------------ exact backward Euler (chord iteration)
+def residual_nonlinear(m: Model, x, v, vn):
+    """Backward-Euler residual of a candidate new velocity vn (Section 5, Eq. 62-63 without the
+    linearisation): R = M (vn - v) - dt (f(x + dt vn) + f_ext) at free vertices, R = vn at pinned ones.
+    R = 0 is the stationarity condition of the incremental potential in the velocity unknown."""
+    R = m.mass[:, None] * (vn - v) - m.dt * (forces(m, x + m.dt * vn) + m.f_ext)
+    R[m.pinned] = vn[m.pinned]
+    return R
+
+
+def step_nonlinear(m: Model, x, v, n_steps=1, max_iters=50, rtol=1e-8):
+    """n_steps backward-Euler steps solved to the nonlinear residual: chord iteration with the constant
+    matrix A = M + dt^2 K, v_0 = 0, v_{k+1} = v_k - A^-1 R(v_k), stopping at the first iterate with
+    ||R(v_k)|| <= rtol ||R(0)|| (or after max_iters solves). The first iterate is the linearised step.
+    Returns (x, v, iterations of each step)."""
+    x = np.array(x, np.float64, copy=True)
+    v = np.array(v, np.float64, copy=True)
+    if m._lu is None:
+        m.A = system_matrix(m)
+        m._lu = spla.splu(m.A)
+    iters = []
+    for _ in range(n_steps):
+        vk = np.zeros_like(v)
+        R = residual_nonlinear(m, x, v, vk)
+        n0 = np.linalg.norm(R)
+        k = 0
+        while k < max_iters:
+            vk = vk - m._lu.solve(R)
+            k += 1
+            R = residual_nonlinear(m, x, v, vk)
+            if np.linalg.norm(R) <= rtol * n0:
+                break
+        iters.append(k)
+        x = x + m.dt * vk
+        v = vk
+    return x, v, iters
+
+
+def incremental_potential(m: Model, x, v, vn):
+    """Incremental potential of the step in the velocity unknown (pinned velocities are zero):
+    E(vn) = 1/2 (vn - v)^T M (vn - v) + Psi(x + dt vn) - f_ext . (x + dt vn); its gradient in vn is
+    M (vn - v) - dt (f(x + dt vn) + f_ext) = R(vn) at free vertices, so backward Euler is its minimiser."""
+    d = vn - v
+    xn = x + m.dt * vn
+    return (0.5 * float(np.sum(m.mass[:, None] * d * d)) + membrane_energy(m, xn) + bending_energy(m, xn)
+            - float(np.sum(m.f_ext * xn)))
