@@ -153,7 +153,8 @@ typedef struct shell_step_stats {
   int64_t total_refine_rounds; /* summed over the call's steps */
   double last_solve_us;        /* device time of the last step's solve of this instance (rhs to commit) */
   int32_t team_ctas;           /* CTAs of the persistent launch that worked on this instance */
-  int32_t pad;
+  int32_t nl_iterations;       /* exact backward Euler (shell_set_nonlinear): chord iterations (solves) of
+                                * the last committed step; 0 for the linearised step */
 } shell_step_stats;
 
 /* ------------------------------------------------------------------------------------------ handle */
@@ -190,6 +191,16 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
 
 /* Energies at the current state, FP64: out[0] membrane, out[1] bending, out[2] kinetic 1/2 v^T M v,
  * out[3] external potential -sum f_ext . (x - X). */
+/* Exact backward Euler (Section 5, Eq. 62-63 without the linearisation): the new velocity v' solves
+ * M (v' - v) = dt (f(x + dt v') + f_ext) at free vertices (v' = 0 at pinned ones), i.e. it minimises the
+ * incremental potential. Each step runs a chord iteration with the constant matrix A = M + dt^2 K: v_0 = 0,
+ * v_{k+1} = v_k - A^-1 R(v_k) with R(v) = M (v - v_t) - dt (f(x_t + dt v) + f_ext), forces re-evaluated at
+ * x_t + dt v_k for every iterate; its first iterate is the linearised step. The step commits the first iterate
+ * with ||R(v_k)|| <= rtol ||R(0)||, or the last of max_iters solves (stats.nl_iterations = max_iters then).
+ * max_iters <= 1 restores the linearised step (the default). Takes effect at the next step of the handle,
+ * alone or in its batch (a batch issues as many force + solve launches per step as its largest max_iters;
+ * finished instances skip the later ones). Errors: INVALID_ARG (max_iters < 0, rtol < 0 or NaN), CUDA. */
+int shell_set_nonlinear(shell_handle *h, int32_t max_iters, double rtol);
 int shell_energy(shell_handle *h, double out[4]);
 
 /* Elastic forces -grad(Psi_m + Psi_b) at the current x in FP64, written to out_xyz [V][3] (host). */

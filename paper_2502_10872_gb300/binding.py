@@ -34,7 +34,8 @@ PRECONDITIONERS = {"auto": 0, "jacobi": 1, "amg": 2}
 
 # symbols declared in include/shell.h
 EXPORTS = (
-    "shell_default_options", "shell_strerror", "shell_create", "shell_step", "shell_step_noalloc", "shell_energy",
+    "shell_default_options", "shell_strerror", "shell_create", "shell_step", "shell_step_noalloc",
+    "shell_set_nonlinear", "shell_energy",
     "shell_forces",
     "shell_apply_matrix", "shell_get_state", "shell_set_state", "shell_get_state_device", "shell_set_state_device", "shell_info",
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
@@ -87,7 +88,7 @@ class shell_step_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int32), ("pcg_iterations", C.c_int32), ("refine_rounds", C.c_int32),
                 ("status", C.c_int32), ("total_pcg_iterations", C.c_int64), ("rel_residual", C.c_double),
                 ("total_refine_rounds", C.c_int64), ("last_solve_us", C.c_double), ("team_ctas", C.c_int32),
-                ("pad", C.c_int32)]
+                ("nl_iterations", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH):
                                    C.POINTER(shell_options), C.POINTER(P)]),
         "shell_step": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
         "shell_step_noalloc": (C.c_int, [P, C.c_int32, C.POINTER(shell_step_stats)]),
+        "shell_set_nonlinear": (C.c_int, [P, C.c_int32, C.c_double]),
         "shell_energy": (C.c_int, [P, P]),
         "shell_forces": (C.c_int, [P, P]),
         "shell_apply_matrix": (C.c_int, [P, P, P]),
@@ -300,6 +302,11 @@ def shell_step(h: Handle, n_steps: int = 1, check: bool = True) -> dict:
     d = st.as_dict()
     d["rc"] = rc
     return d
+
+
+def shell_set_nonlinear(h: Handle, max_iters: int, rtol: float = 1e-8):
+    """Exact backward Euler by chord iteration: up to max_iters solves per step (<= 1: linearised step)."""
+    _check(load_library().shell_set_nonlinear(h.ptr, int(max_iters), float(rtol)), "shell_set_nonlinear")
 
 
 def shell_step_noalloc(h: Handle, n_steps: int = 1, check: bool = True) -> dict:

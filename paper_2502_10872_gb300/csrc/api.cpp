@@ -174,6 +174,7 @@ struct shell_batch {
   bool cluster_off = false;    // set if a cluster launch was refused
   int policy = 0;              // 0 flat teams, 1 one-cluster teams
   int occ_launch = 3;          // occupancy variant of the current plan
+  int chord_max = 1;           // solve launches per step (exact backward Euler: the largest nl_max)
   double plan_T = 0.0;         // makespan the current flat plan was built for (ns, or model units)
   double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
@@ -221,6 +222,8 @@ int rebuild_tables(shell_batch *b) {
     if (b->slots[k]) b->active.push_back((int)k);
   const int n = (int)b->active.size();
   b->n_active = n;
+  b->chord_max = 1;
+  for (int k : b->active) b->chord_max = std::max(b->chord_max, b->slots[k]->h.nl_max);
   if (n == 0) {
     b->dirty = false;
     return SHELL_OK;
@@ -461,7 +464,8 @@ int rebuild_tables(shell_batch *b) {
 
 // the solve launch; if the driver refuses the cluster launch, fall back to plain global team barriers (the
 // team layout stays valid: whole-cluster teams become flat global-barrier teams)
-cudaError_t solve_launch(shell_batch *b, cudaStream_t st) {
+cudaError_t solve_launch(shell_batch *b, cudaStream_t st, int chord_k) {
+  b->sched.chord_k = chord_k;
   cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, b->occ_launch, st);
   if (e != cudaSuccess && b->sched.cluster > 0) {
     cudaGetLastError();
@@ -472,11 +476,15 @@ cudaError_t solve_launch(shell_batch *b, cudaStream_t st) {
   return e;
 }
 
+// one step: forces and solve, repeated for the chord iterations of exact backward-Euler instances
+// (instances whose step is done skip the later launches)
 int launch_step(shell_batch *b) {
   cudaStream_t st = b->mem.st;
-  CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
-  CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
-  CK(solve_launch(b, st));
+  for (int k = 0; k < b->chord_max; ++k) {
+    CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));
+    CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st, k));
+    CK(solve_launch(b, st, k));
+  }
   return SHELL_OK;
 }
 
@@ -542,8 +550,13 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
       CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
       CK(cudaEventRecord(b->pev[3 * s + 1], st));
-      CK(solve_launch(b, st));
+      CK(solve_launch(b, st, 0));
       CK(cudaEventRecord(b->pev[3 * s + 2], st));
+      for (int k = 1; k < b->chord_max; ++k) {   // later chord iterations (not split by the profile)
+        CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));
+        CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st, k));
+        CK(solve_launch(b, st, k));
+      }
     } else if (b->gexec) {
       CK(cudaGraphLaunch(b->gexec, st));
     } else {
@@ -613,6 +626,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       o.total_refine_rounds = a.total_rounds - z.total_rounds;
       o.last_solve_us = a.last_ns * 1e-3;
       o.team_ctas = a.team_size;
+      o.nl_iterations = h->h.nl_max > 1 ? a.nl_iters : 0;
     }
   }
   return first_err;
@@ -976,6 +990,8 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   I.n_chunks = (nv + chunk - 1) / chunk;
   I.pcg_max_it = opt.pcg_max_it;
   I.refine_max = opt.refine_max;
+  I.nl_max = 0;        // linearised step until shell_set_nonlinear
+  I.nl_rtol = 1e-8;
   I.dt = opt.dt;
   I.pcg_rtol = opt.pcg_rtol;
   I.refine_rtol = opt.refine_rtol;
@@ -1000,6 +1016,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.x = C.take<double>(3 * (size_t)nv);
     I.v = C.take<double>(3 * (size_t)nv);
     I.vprev = C.take<double>(3 * (size_t)nv);
+    I.xk = C.take<double>(3 * (size_t)nv);
     I.rest = C.take<double>(3 * (size_t)nv);
     I.fext = C.take<double>(3 * (size_t)nv);
     I.mass = C.take<double>(nv);
@@ -1209,7 +1226,7 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
   InstStatus after{};
   int32_t aborted = 0;
   cudaError_t e = launch_step_static(h->d_inst, h->d_tiles, (int)h->tiles.size(), h->h.precision != SHELL_FP64, team,
-                                     n_steps, &after, &aborted, h->mem.st);
+                                     n_steps, std::max(1, h->h.nl_max), &after, &aborted, h->mem.st);
   if (e != cudaSuccess) {
     last_cuda_error() = e;
     return SHELL_ERR_CUDA;
@@ -1225,6 +1242,7 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
     stats->total_refine_rounds = after.total_rounds - before.total_rounds;
     stats->last_solve_us = after.last_ns * 1e-3;
     stats->team_ctas = after.team_size;
+    stats->nl_iterations = h->h.nl_max > 1 ? after.nl_iters : 0;
   }
   if (aborted) return SHELL_ERR_TIMEOUT;
   return after.err;
@@ -1237,6 +1255,19 @@ static int run_forces64(shell_handle *h, int want_energy) {
     last_cuda_error() = e;
     return SHELL_ERR_CUDA;
   }
+  return SHELL_OK;
+}
+
+// exact backward Euler: chord iterations per step (<= 1: linearised step) and their tolerance
+int shell_set_nonlinear(shell_handle *h, int32_t max_iters, double rtol) {
+  if (!h || max_iters < 0 || !(rtol >= 0.0)) return SHELL_ERR_INVALID_ARG;
+  h->h.nl_max = max_iters;
+  h->h.nl_rtol = rtol;
+  CK(cudaMemcpyAsync(h->d_inst, &h->h, sizeof(Inst), cudaMemcpyHostToDevice, h->mem.st));
+  CK(cudaStreamSynchronize(h->mem.st));
+  // batches hold copies of the descriptor and plan their launches per step by it
+  if (h->batch) h->batch->dirty = true;
+  if (h->solo) h->solo->dirty = true;
   return SHELL_OK;
 }
 

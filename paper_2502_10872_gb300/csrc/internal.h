@@ -41,6 +41,10 @@ struct InstStatus {
   long long total_rounds;
   long long last_ns;    // device time of the last step's solve of this instance (right-hand side to commit)
   long long max_ns;     // longest solve time since the status was last gathered (the gather resets it)
+  int32_t nl_flags;     // bit 0: a step's chord iteration is in progress; bit 1: last step stopped at nl_max
+  int32_t nl_iters;     // chord iterations of the step in progress / of the last committed step
+  double nl_r0;         // ||R(0)||^2 of the step in progress (= ||b||^2 of its first solve)
+  long long nl_step_pcg;  // PCG iterations summed over the chord iterations of the step in progress
 };
 
 // Per-block gather lists of a SELL-32 matrix (device pointers): block b = rows [256 b, 256 b + 256) stages the
@@ -88,13 +92,15 @@ struct Inst {
   int32_t rows_per_thread;       // rows per thread of a reduction chunk (chunk = kBlock * rows_per_thread)
   int32_t n_chunks;
   int32_t pcg_max_it, refine_max;
-  int32_t pad0;
+  int32_t nl_max;                // chord iterations per step of the exact backward Euler (<= 1: linearised step)
   double dt, pcg_rtol, refine_rtol;
+  double nl_rtol;                // chord stop: ||R(v_k)|| <= nl_rtol ||R(0)||
   double mu, lam;                // membrane Lame parameters (plane stress)
 
   // state (FP64, SoA [3][nv])
   double *x, *v, *rest, *fext;
   double *vprev;                 // velocity before the last committed step (warm-start extrapolation)
+  double *xk;                    // [3][nv] chord iterate x + dt v_k, where the next forces are evaluated
   double *mass;                  // [nv]
   uint8_t *pinned;               // [nv]
 
@@ -186,15 +192,16 @@ struct Sched {
   int32_t n_ctas;
   int32_t cluster;       // CTAs per cluster of the launch, 0 = no clusters
   int32_t halo_cap;      // vector entries the launch's dynamic shared memory stages (set by launch_solve)
-  int32_t pad;
+  int32_t chord_k;       // chord iteration of the step this launch performs (0: the first, or the only one)
 };
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)
 cudaError_t launch_precompute(const Inst *d_inst, const Inst &h_inst, double E, double nu, double thickness,
                               double density, cudaStream_t st);
 cudaError_t launch_assemble(const Inst *d_inst, const Inst &h_inst, cudaStream_t st);
+// chord_k > 0: only instances in a chord iteration, at their iterate positions xk
 cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles, int want_energy, int fp32,
-                          cudaStream_t st);
+                          cudaStream_t st, int chord_k = 0);
 cudaError_t launch_gather_forces(const Inst *d_inst, const Inst &h_inst, double *d_out, cudaStream_t st);
 cudaError_t launch_energy_reduce(const Inst *d_inst, const Inst &h_inst, double *d_out4, cudaStream_t st);
 cudaError_t launch_solve(const Inst *d_insts, const Sched &sched, int grid, int prec, int occ, cudaStream_t st);
@@ -213,6 +220,7 @@ int solve_max_clusters(int prec, int cluster);   // co-resident clusters of the 
 constexpr int kCluster = 8;                      // cluster size of the batched solve launch (portable)
 int static_max_ctas();
 cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
-                               int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st);
+                               int n_steps, int chord_launches, InstStatus *h_status, int32_t *h_aborted,
+                               cudaStream_t st);
 
 }  // namespace shl

@@ -55,19 +55,22 @@ __device__ inline double rsqrt_<double>(double a) { return 1.0 / sqrt(a); }
 // precision-specific views of the stencil data
 template <typename R>
 struct Data;
+// X: the positions the forces are evaluated at (x, or the chord iterate xk)
 template <>
 struct Data<double> {
   const double *tL, *tW, *tk0, *tn, *mD, *mAt, *eL, *ew, *ek0, *en;
-  __device__ Data(const Inst &I)
+  const double *X;
+  __device__ Data(const Inst &I, const double *pos)
       : tL(I.t_L64), tW(I.t_W64), tk0(I.t_k064), tn(I.t_n64), mD(I.m_D64), mAt(I.m_At64), eL(I.e_L64),
-        ew(I.e_w64), ek0(I.e_k064), en(I.e_n64) {}
+        ew(I.e_w64), ek0(I.e_k064), en(I.e_n64), X(pos) {}
 };
 template <>
 struct Data<float> {
   const float *tL, *tW, *tk0, *tn, *mD, *mAt, *eL, *ew, *ek0, *en;
-  __device__ Data(const Inst &I)
+  const double *X;
+  __device__ Data(const Inst &I, const double *pos)
       : tL(I.t_L32), tW(I.t_W32), tk0(I.t_k032), tn(I.t_n32), mD(I.m_D32), mAt(I.m_At32), eL(I.e_L32),
-        ew(I.e_w32), ek0(I.e_k032), en(I.e_n32) {}
+        ew(I.e_w32), ek0(I.e_k032), en(I.e_n32), X(pos) {}
 };
 
 struct dpos {
@@ -95,13 +98,13 @@ __device__ void tri_stencil(const Inst &I, const Data<R> &D, int t, bool want_en
   const int nloc = bend ? 6 : 3;
   int idx[6];
   for (int j = 0; j < nloc; ++j) idx[j] = I.t_idx[j * nt + t];
-  const dpos o = loadx(I.x, nv, idx[0]);
+  const dpos o = loadx(D.X, nv, idx[0]);
   dpos xd[3];
   v3<R> d[6];
   d[0] = zero3<R>();
   for (int j = 1; j < nloc; ++j) {
     if (idx[j] >= 0) {
-      dpos xj = loadx(I.x, nv, idx[j]);
+      dpos xj = loadx(D.X, nv, idx[j]);
       if (j < 3) xd[j] = {xj.x - o.x, xj.y - o.y, xj.z - o.z};
       d[j] = diff<R>(xj, o);
     } else {
@@ -219,12 +222,12 @@ __device__ void edge_stencil(const Inst &I, const Data<R> &D, int e, bool want_e
   const int ne = I.ne, nv = I.nv;
   int idx[4];
   for (int j = 0; j < 4; ++j) idx[j] = I.e_idx[j * ne + e];
-  const dpos o = loadx(I.x, nv, idx[1]);
+  const dpos o = loadx(D.X, nv, idx[1]);
   v3<R> d[4];
   d[1] = zero3<R>();
-  d[0] = diff<R>(loadx(I.x, nv, idx[0]), o);
-  d[2] = diff<R>(loadx(I.x, nv, idx[2]), o);
-  d[3] = idx[3] >= 0 ? diff<R>(loadx(I.x, nv, idx[3]), o) : zero3<R>();
+  d[0] = diff<R>(loadx(D.X, nv, idx[0]), o);
+  d[2] = diff<R>(loadx(D.X, nv, idx[2]), o);
+  d[3] = idx[3] >= 0 ? diff<R>(loadx(D.X, nv, idx[3]), o) : zero3<R>();
   R L[4];
   for (int j = 0; j < 4; ++j) L[j] = D.eL[j * ne + e];
   const R w = D.ew[e];
@@ -297,15 +300,18 @@ __device__ void edge_stencil(const Inst &I, const Data<R> &D, int e, bool want_e
   }
 }
 
+// chord_k > 0: a later chord iteration of the exact backward-Euler step; only instances whose step is in a
+// chord iteration take part, with forces at their iterate positions xk
 template <typename R>
 __global__ void __launch_bounds__(kForceBlock) k_forces(const Inst *__restrict__ insts, const Tile *__restrict__ tiles,
-                                                        int want_energy) {
+                                                        int want_energy, int chord_k) {
   const Tile tl = tiles[blockIdx.x];
   const Inst &I = insts[tl.inst];
   if (!want_energy && I.status->err != SHELL_OK) return;
+  if (chord_k > 0 && !(I.status->nl_flags & 1)) return;
   if ((int)threadIdx.x >= tl.count) return;
   const int s = tl.first + threadIdx.x;
-  const Data<R> D(I);
+  const Data<R> D(I, chord_k > 0 ? I.xk : I.x);
   if (tl.kind == 0)
     tri_stencil<R>(I, D, s, want_energy != 0);
   else
@@ -439,12 +445,12 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
 }
 
 cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles, int want_energy, int fp32,
-                          cudaStream_t st) {
+                          cudaStream_t st, int chord_k) {
   if (n_tiles <= 0) return cudaSuccess;
   if (fp32)
-    k_forces<float><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy);
+    k_forces<float><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy, chord_k);
   else
-    k_forces<double><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy);
+    k_forces<double><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy, chord_k);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,7 @@ struct Team {
   int *cluster_ok;
   unsigned long long t0;   // start of the current instance's solve (global timer, ns)
   int cap;      // vector entries the dynamic shared memory can stage (0: no staging)
+  int chord_k;  // chord iteration of the step this launch performs
 };
 
 __device__ inline void cluster_barrier() {
@@ -487,9 +488,13 @@ __device__ __forceinline__ void staged_row64(const HaloDev &H, int blk, const D4
   }
 
 // b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = 2 v - v_prev; g64 = sol; partial ||b||^2
+// Chord iteration k > 0 of the exact backward-Euler step (forces at x + dt v_k, v_k in sol and g64):
+// b = M v + dt (f + f_ext) + (A - M) v_k, warm start v_k kept, so that the first residual b - A v_k is
+// -R(v_k), the backward-Euler residual, and the solve gives v_{k+1} = v_k - A^-1 R(v_k).
 template <typename RC>
 __device__ void phase_rhs(const Inst &I, const Team &tm) {
   const int nv = I.nv;
+  const bool chord = tm.chord_k > 0;
   const RC *con = reinterpret_cast<const RC *>(I.contrib);
   ChunkStage cs;
   for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
@@ -506,18 +511,23 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
       }
       const bool pin = I.pinned[row] != 0;
       const double m = I.mass[row];
+      double av[3] = {0.0, 0.0, 0.0};
+      if (chord) spmv_row(I, I.val64, reinterpret_cast<const D4 *>(I.g64), row, av[0], av[1], av[2]);
       double sv[3];
       for (int c = 0; c < 3; ++c) {
         const double v = I.v[c * nv + row];
         double b = m * v + I.dt * (f[c] + I.fext[c * nv + row]);
+        if (chord) b += av[c] - m * I.sol[c * nv + row];
         if (pin) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
         // initial guess: linear extrapolation of the last two velocities (v after a state is set)
-        sv[c] = pin ? 0.0 : 2.0 * v - I.vprev[c * nv + row];
-        I.sol[c * nv + row] = sv[c];
+        if (!chord) {
+          sv[c] = pin ? 0.0 : 2.0 * v - I.vprev[c * nv + row];
+          I.sol[c * nv + row] = sv[c];
+        }
       }
-      reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
+      if (!chord) reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
     }
     stage_chunk<double>(cs, I, tm, ch, bb, 0.0, 0.0);
   }
@@ -1308,6 +1318,20 @@ __device__ void phase_commit(const Inst &I, const Team &tm) {
   ROWS_END
 }
 
+// hand-off to the next chord iteration: xk = x + dt sol (where the next forces are evaluated), g64 = sol
+__device__ void phase_chord(const Inst &I, const Team &tm) {
+  const int nv = I.nv;
+  ROWS_BEGIN(I, tm)
+  double sv[3];
+  for (int c = 0; c < 3; ++c) {
+    const int k = c * nv + row;
+    sv[c] = I.sol[k];
+    I.xk[k] = I.x[k] + I.dt * sv[c];
+  }
+  reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
+  ROWS_END
+}
+
 __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, int rounds, double rel) {
   if (tm.rank == 0 && threadIdx.x == 0) {
     InstStatus *s = I.status;
@@ -1327,12 +1351,56 @@ __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, in
       s->last_iters = iters;
       s->last_rounds = rounds;
       s->rel_res = rel;
+      s->nl_flags = 0;
     }
   }
 }
 
-// returns false if the kernel must stop (abort)
+// End of one solve of a step. Linearised step (nl_max <= 1): commit v, x. Exact backward Euler: commit
+// when the chord iteration met its tolerance before this solve (done_early) or used its nl_max solves,
+// else hand off to the next iteration. bb: ||b||^2 of this solve (at k = 0: ||R(0)||^2).
+__device__ void finish_step(const Inst &I, const Team &tm, double bb, int iters, int rounds, double rel,
+                            bool done_early) {
+  const int k = tm.chord_k;
+  if (I.nl_max <= 1) {
+    phase_commit(I, tm);
+    set_status(I, tm, SHELL_OK, iters, rounds, rel);
+    return;
+  }
+  const int solves = done_early ? k : k + 1;
+  const bool last = done_early || solves >= I.nl_max;
+  if (last)
+    phase_commit(I, tm);
+  else
+    phase_chord(I, tm);
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    InstStatus *s = I.status;
+    const long long step_pcg = (k == 0 ? 0 : s->nl_step_pcg) + iters;
+    s->last_ns = (long long)(gtimer() - tm.t0);
+    s->max_ns = s->last_ns > s->max_ns ? s->last_ns : s->max_ns;
+    s->team_size = tm.size;
+    s->total_iters += iters;
+    s->total_rounds += rounds;
+    s->nl_iters = solves;
+    if (k == 0) s->nl_r0 = bb;
+    if (last) {
+      s->steps_done += 1;
+      s->last_iters = (int)step_pcg;
+      s->last_rounds = rounds;
+      s->rel_res = rel;
+      s->nl_flags = done_early ? 0 : 2;
+    } else {
+      s->nl_step_pcg = step_pcg;
+      s->nl_flags = 1;
+    }
+  }
+}
+
+// returns false if the kernel must stop (abort). Chord iteration k > 0 of an exact backward-Euler step: the
+// first residual of the solve is the backward-Euler residual R(v_k); if it meets nl_rtol ||R(0)|| the step
+// commits v_k without solving, else the solve's tolerance refers to it.
 __device__ bool solve_fp64(const Inst &I, Team &tm) {
+  const int k = tm.chord_k;
   phase_rhs<double>(I, tm);
   if (!team_sync(tm)) return false;
   double red[3];
@@ -1343,16 +1411,31 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
     return true;
   }
   int iters = 0;
-  double rho = 0.0;
+  double rho = 0.0, ref = bb;
+  bool early = false;
   if (bb > 0.0) {
     phase_resid<double>(I, tm);   // r = b - A sol, g = D^-1 r
-    const double tol2 = I.pcg_rtol * I.pcg_rtol * bb;
-    iters = cg_loop<double>(I, tm, I.sol, tol2, I.pcg_max_it, &rho);
-    if (iters == -2) return false;
-    if (iters < 0) {
-      set_status(I, tm, iters == -1 ? SHELL_ERR_NOT_CONVERGED : SHELL_ERR_NONFINITE, I.pcg_max_it, 0,
-                 sqrt(rho / bb));
-      return true;
+    if (k > 0) {
+      if (!team_sync(tm)) return false;
+      team_reduce(I, tm, red);
+      rho = red[0];
+      if (!isfinite(rho)) {
+        set_status(I, tm, SHELL_ERR_NONFINITE, 0, 0, 0.0);
+        return true;
+      }
+      const double r0 = __ldcg(&I.status->nl_r0);
+      early = rho <= I.nl_rtol * I.nl_rtol * r0;
+      ref = early ? r0 : rho;
+    }
+    if (!early) {
+      const double tol2 = I.pcg_rtol * I.pcg_rtol * ref;
+      iters = cg_loop<double>(I, tm, I.sol, tol2, I.pcg_max_it, &rho);
+      if (iters == -2) return false;
+      if (iters < 0) {
+        set_status(I, tm, iters == -1 ? SHELL_ERR_NOT_CONVERGED : SHELL_ERR_NONFINITE, I.pcg_max_it, 0,
+                   sqrt(rho / ref));
+        return true;
+      }
     }
   } else {
     // b = 0: the solution is v' = 0
@@ -1360,12 +1443,12 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
     for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
     ROWS_END
   }
-  phase_commit(I, tm);
-  set_status(I, tm, SHELL_OK, iters, 0, bb > 0.0 ? sqrt(rho / bb) : 0.0);
+  finish_step(I, tm, bb, iters, 0, ref > 0.0 ? sqrt(rho / ref) : 0.0, early);
   return true;
 }
 
 __device__ bool solve_fp32r(const Inst &I, Team &tm) {
+  const int k = tm.chord_k;
   phase_rhs<float>(I, tm);
   if (!team_sync(tm)) return false;
   double red[3];
@@ -1376,20 +1459,31 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
     return true;
   }
   int total = 0, rounds = 0;
-  double rel = 0.0;
+  double rel = 0.0, ref = bb;
+  bool early = false;
   if (bb > 0.0) {
-    const double tol_ref2 = I.refine_rtol * I.refine_rtol * bb;
+    double tol_ref2 = I.refine_rtol * I.refine_rtol * bb;
     const double tin2 = I.pcg_rtol * I.pcg_rtol;
     for (;;) {
       phase_resid<float>(I, tm);
       if (!team_sync(tm)) return false;
       team_reduce(I, tm, red);
       const double r2 = red[0];
-      rel = sqrt(r2 / bb);
       if (!isfinite(r2)) {
-        set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
+        set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, sqrt(r2 / ref));
         return true;
       }
+      if (rounds == 0 && k > 0) {   // chord: r2 = ||R(v_k)||^2
+        const double r0 = __ldcg(&I.status->nl_r0);
+        if (r2 <= I.nl_rtol * I.nl_rtol * r0) {
+          early = true;
+          rel = r0 > 0.0 ? sqrt(r2 / r0) : 0.0;
+          break;
+        }
+        ref = r2;
+        tol_ref2 = I.refine_rtol * I.refine_rtol * r2;
+      }
+      rel = sqrt(r2 / ref);
       if (r2 <= tol_ref2) break;
       if (rounds >= I.refine_max) {
         set_status(I, tm, SHELL_ERR_NOT_CONVERGED, total, rounds, rel);
@@ -1415,8 +1509,7 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
     for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
     ROWS_END
   }
-  phase_commit(I, tm);
-  set_status(I, tm, SHELL_OK, total, rounds, rel);
+  finish_step(I, tm, bb, total, rounds, rel, early);
   return true;
 }
 
@@ -1436,6 +1529,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
   tm.cluster = sch.cluster;
   tm.cluster_ok = sch.cluster_ok;
   tm.cap = sch.halo_cap;
+  tm.chord_k = sch.chord_k;
   if (tm.size == 1)
     tm.mode = 0;
   else if (sch.cluster > 0 && tm.size % sch.cluster == 0)
@@ -1445,6 +1539,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
   for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
     const Inst &I = insts[sch.team_list[q]];
     if (I.status->err != SHELL_OK) continue;
+    if (sch.chord_k > 0 && !(I.status->nl_flags & 1)) continue;   // no chord iteration in progress
     tm.t0 = gtimer();
     bool ok;
     if (PREC == 1 || (PREC == 0 && I.precision == SHELL_FP64))
@@ -1586,7 +1681,8 @@ cudaError_t static_scratch_setup(unsigned int **out) {
 int static_max_ctas() { return kStaticMaxCtas; }
 
 cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
-                               int n_steps, InstStatus *h_status, int32_t *h_aborted, cudaStream_t st) {
+                               int n_steps, int chord_launches, InstStatus *h_status, int32_t *h_aborted,
+                               cudaStream_t st) {
   unsigned int *base = nullptr;
   cudaError_t e = static_scratch_setup(&base);
   if (e != cudaSuccess) return e;
@@ -1623,9 +1719,12 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
     return e;
   // the barrier words and the abort flag must start at zero; the array keeps the previous call's contents
   if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (kBarWords + 2), st)) != cudaSuccess) return e;
-  for (int k = 0; k < n_steps; ++k) {
-    if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st)) != cudaSuccess) return e;
-    if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, 3, st)) != cudaSuccess) return e;
+  for (int step = 0; step < n_steps; ++step) {
+    for (int k = 0; k < chord_launches; ++k) {   // chord iterations of an exact backward-Euler step
+      if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st, k)) != cudaSuccess) return e;
+      sc.chord_k = k;
+      if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, 3, st)) != cudaSuccess) return e;
+    }
   }
   if ((e = launch_gather_status(d_inst, 1, status_out, sc.abort_flag, abort_out, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(h_status, status_out, sizeof(InstStatus), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
