@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=120.0)
+    ap.add_argument("--nonlinear", default=None,
+                    help="K,RTOL: exact backward Euler (chord iteration, up to K solves per step, stop at "
+                         "||R|| <= RTOL ||R(0)||) instead of the linearised step, for every instance")
     ap.add_argument("--launch", default=None,
                     help="CTAS_PER_SM,SHARE,CLUSTERS: apply this solve-launch shape to the FP32 batch instead of "
                          "autotuning (e.g. the shape a plain run chose, for a profiler run whose timings would "
@@ -295,6 +298,10 @@ def main():
 
     def make_batch(precision):
         hs = [gb.create_from_scenario(sc, precision=precision) for sc in scs]
+        if args.nonlinear:
+            kk, rt = args.nonlinear.split(",")
+            for h in hs:
+                gb.shell_set_nonlinear(h, int(kk), float(rt))
         b = gb.shell_batch_create(1 << 50)
         for h in hs:
             gb.shell_batch_admit(b, h)
@@ -399,6 +406,7 @@ def main():
                "seconds": round(secs, 2)}
 
     iters = [s["total_pcg_iterations"] / K for s in stats32.values()]
+    chord = [s["nl_iterations"] for s in stats32.values()]
     rounds = [s["total_refine_rounds"] / K for s in stats32.values()]
     line = {
         "metric": METRIC, "value": value, "unit": "vertex-steps/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -411,6 +419,9 @@ def main():
         "latency_ms": {"p50": p50, "p99": p99},
         "autotune": tuned,
         "fp64": fp64, "accuracy": acc,
+        "integrator": ("linearised backward Euler" if not args.nonlinear else
+                       f"exact backward Euler (chord iteration, K,rtol = {args.nonlinear}); mean chord "
+                       f"iterations in the last step {float(np.mean(chord)):.2f}"),
         "solver": {"mean_inner_iterations_per_step": float(np.mean(iters)),
                    "max_inner_iterations_per_step": float(np.max(iters)),
                    "mean_refine_rounds_per_step": float(np.mean(rounds))},
