@@ -263,7 +263,8 @@ int shell_batch_state_layout(shell_batch *b, int32_t *slots, int64_t *row_offset
 /* Device time of the last shell_batch_step, per step, in milliseconds: out[k] for k < n (n <= steps). */
 int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
 /* Kernel timing of later shell_batch_step calls: with on != 0 every step is launched directly (not from
- * the graph) with CUDA events around the force launches and the solve launch. shell_batch_kernel_times
+ * the graph) with CUDA events around the force launches and the solve launch (of every chord iteration of
+ * an exact backward-Euler step). shell_batch_kernel_times
  * then gives out_ms[0] = summed force-kernel time and out_ms[1] = summed solve-kernel time of the last
  * call, in milliseconds. */
 int shell_batch_set_profiling(shell_batch *b, int32_t on);

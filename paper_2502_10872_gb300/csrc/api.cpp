@@ -538,24 +538,24 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   const int ev_stride = (n_steps + n_ev - 2) / (n_ev - 1);
   int ev = 0;
   CK(cudaEventRecord(b->events[ev++], st));
-  const int n_prof = b->profiling ? std::min(n_steps, 4096) : 0;
-  while ((int)b->pev.size() < 3 * n_prof) {
+  // profiled steps: events around the force launches and the solve launch of every chord iteration
+  const int n_prof = b->profiling ? std::min(n_steps, std::max(1, 4096 / b->chord_max)) : 0;
+  const int pev_per_step = 3 * b->chord_max;
+  while ((int)b->pev.size() < pev_per_step * n_prof) {
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
     b->pev.push_back(e);
   }
   for (int s = 0; s < n_steps; ++s) {
     if (s < n_prof) {
-      CK(cudaEventRecord(b->pev[3 * s], st));
-      CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st));
-      CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st));
-      CK(cudaEventRecord(b->pev[3 * s + 1], st));
-      CK(solve_launch(b, st, 0));
-      CK(cudaEventRecord(b->pev[3 * s + 2], st));
-      for (int k = 1; k < b->chord_max; ++k) {   // later chord iterations (not split by the profile)
+      for (int k = 0; k < b->chord_max; ++k) {
+        const int e0 = pev_per_step * s + 3 * k;
+        CK(cudaEventRecord(b->pev[e0], st));
         CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));
         CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st, k));
+        CK(cudaEventRecord(b->pev[e0 + 1], st));
         CK(solve_launch(b, st, k));
+        CK(cudaEventRecord(b->pev[e0 + 2], st));
       }
     } else if (b->gexec) {
       CK(cudaGraphLaunch(b->gexec, st));
@@ -571,7 +571,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   CK(cudaMemcpyAsync(&aborted, b->d_abort_out, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   b->kern_ms[0] = b->kern_ms[1] = 0.0;
-  for (int s = 0; s < n_prof; ++s) {
+  for (int s = 0; s < n_prof * b->chord_max; ++s) {
     float f = 0.f, v = 0.f;
     cudaEventElapsedTime(&f, b->pev[3 * s], b->pev[3 * s + 1]);
     cudaEventElapsedTime(&v, b->pev[3 * s + 1], b->pev[3 * s + 2]);
