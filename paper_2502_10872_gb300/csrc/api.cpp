@@ -1331,7 +1331,6 @@ int shell_set_state(shell_handle *h, const double *x, const double *v) {
   if (v) {
     CK(cudaMemcpyAsync(h->d_stage + n3, v, 8 * n3, cudaMemcpyHostToDevice, st));
     CK(launch_aos_to_soa(h->d_stage + n3, h->h.v, h->nv, st));
-    CK(cudaMemcpyAsync(h->h.vprev, h->h.v, 8 * n3, cudaMemcpyDeviceToDevice, st));
   }
   // a new state clears a previous step failure
   CK(cudaMemsetAsync(&h->h.status->err, 0, sizeof(int32_t), st));
@@ -1352,10 +1351,7 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
   if (!h) return SHELL_ERR_INVALID_ARG;
   cudaStream_t st = h->mem.st;
   if (d_x) CK(launch_aos_to_soa(d_x, h->h.x, h->nv, st));
-  if (d_v) {
-    CK(launch_aos_to_soa(d_v, h->h.v, h->nv, st));
-    CK(cudaMemcpyAsync(h->h.vprev, h->h.v, 24 * (size_t)h->nv, cudaMemcpyDeviceToDevice, st));
-  }
+  if (d_v) CK(launch_aos_to_soa(d_v, h->h.v, h->nv, st));
   return SHELL_OK;
 }
 

@@ -407,7 +407,6 @@ __global__ void k_pack_states(const Inst *__restrict__ insts, int n, const long 
     if (unpack) {
       I.x[c * I.nv + i] = x[3 * row + c];
       I.v[c * I.nv + i] = v[3 * row + c];
-      I.vprev[c * I.nv + i] = v[3 * row + c];
     } else {
       x[3 * row + c] = I.x[c * I.nv + i];
       v[3 * row + c] = I.v[c * I.nv + i];

@@ -521,7 +521,8 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
         if (pin) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
-        // initial guess: linear extrapolation of the last two velocities (v after a state is set)
+        // initial guess: linear extrapolation of the last two velocities (v_prev: the velocity before the
+        // last committed step; setting a state leaves it, as it only shapes the initial guess)
         if (!chord) {
           sv[c] = pin ? 0.0 : 2.0 * v - I.vprev[c * nv + row];
           I.sol[c * nv + row] = sv[c];

@@ -315,3 +315,27 @@ def test_shared_memory_staging_is_bitwise_neutral(case):
     assert max(levels) >= 3     # the multigrid path (coarse lists) is exercised
     for (xa, va), (xb, vb) in zip(*out):
         assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+
+
+def test_state_round_trip_leaves_steps_bitwise_unchanged():
+    """Reading the states and writing them back between steps (packed batch transfer, or per handle) changes
+    nothing: the next steps equal those of an untouched batch bitwise (the warm start's velocity history is
+    kept)."""
+    scs = sg.mixed_batch(4, seed=52, side_lo=6, side_hi=30)
+    out = []
+    for round_trip in (False, True):
+        b = gb.shell_batch_create(1 << 40)
+        hs = [gb.create_from_scenario(sc, precision="fp32_refine") for sc in scs]
+        for h in hs:
+            gb.shell_batch_admit(b, h)
+        for _ in range(4):
+            if round_trip:
+                x, v = gb.shell_batch_get_states(b)
+                gb.shell_batch_set_states(b, x, v)
+                xa, va = gb.shell_get_state(hs[0])
+                gb.shell_set_state(hs[0], xa, va)
+            gb.shell_batch_step(b, 1)
+        out.append([gb.shell_get_state(h) for h in hs])
+        gb.shell_batch_destroy(b)
+    for (xa, va), (xb, vb) in zip(*out):
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb)
