@@ -7,6 +7,9 @@
 //               nodes join a neighbouring aggregate; the rest form their own
 //   P           (I - omega D^-1 A) P0, P0 the aggregate indicator (near-null space: constants), omega = 4/(3 rho)
 //   A_c         P^T A P (Galerkin), repeated until the level is small; the coarsest is inverted densely
+//   dense end   from the first level of at most dense_max rows down, the cycle (started from zero) is a fixed
+//               linear map of that level's right-hand side: stored as a dense matrix, built by applying the
+//               same steps to the unit vectors
 #include "amg_setup.h"
 
 #include <algorithm>

@@ -707,7 +707,9 @@ std::vector<double> to_soa(const double *aos, int nv) {
 }
 
 // Multigrid preconditioner: download the assembled FP64 matrix, build the smoothed-aggregation hierarchy
-// on the host (the matrix is constant, so this happens once) and upload it as SELL-32 levels.
+// on the host (the matrix is constant, so this happens once) and upload its levels: P in SELL-32, R and the
+// coarse operators with 4 lanes per row, the dense operator of the coarse end of the cycle, and (FP32
+// instances) the gather lists of every product.
 int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   Inst &I = h->h;
   cudaStream_t st = h->mem.st;

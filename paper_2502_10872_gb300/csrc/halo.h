@@ -1,4 +1,4 @@
-// halo.h -- per-block gather lists of a SELL-32 matrix, for products that stage the gathered vector in
+// halo.h -- per-block gather lists of a SELL matrix, for products that stage the gathered vector in
 // shared memory (host, once per matrix).
 //
 // Block b is the rows one CTA processes together: 256 (one lane per row) or 64 (four lanes per row). Its list holds, in

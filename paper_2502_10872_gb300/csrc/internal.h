@@ -47,10 +47,10 @@ struct InstStatus {
   long long nl_step_pcg;  // PCG iterations summed over the chord iterations of the step in progress
 };
 
-// Per-block gather lists of a SELL-32 matrix (device pointers): block b = rows [256 b, 256 b + 256) stages the
-// vector entries col[b * max .. b * max + max) in shared memory (lists padded to the longest, max); c16 is
-// each stored entry's index into its block's list; own[b] is the local index of the block's first row
-// (square matrices). max = 0: no lists.
+// Per-block gather lists of a SELL matrix (device pointers): block b (256 rows, or 64 rows for matrices with 4
+// lanes per row) stages the vector entries col[b * max .. b * max + max) in shared memory (lists padded to
+// the longest, max); c16 is each stored entry's index into its block's list; own[b] is the local index of
+// the block's first row (square matrices). max = 0: no lists.
 struct HaloDev {
   int32_t *col, *own;
   uint16_t *c16;

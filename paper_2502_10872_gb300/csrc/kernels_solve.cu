@@ -1,7 +1,11 @@
-// kernels_solve.cu -- persistent per-step solve: right-hand side, Jacobi-preconditioned conjugate
-// gradients on the constant matrix, state update. One launch per step serves every instance of a batch.
+// kernels_solve.cu -- persistent per-step solve: right-hand side, preconditioned conjugate gradients on the
+// constant matrix (Jacobi, or a smoothed-aggregation multigrid V-cycle whose coarse end is one dense
+// operator), state update. One launch per step serves every instance of a batch.
 //
 // Step (Section 5, Eq. 62-63, linearised): (M + dt^2 K) v' = M v + dt (f + f_ext); x' = x + dt v'.
+// Exact backward Euler (optional, per instance): the same launch repeated as a chord iteration, each with
+// the forces at the previous iterate (phase_rhs, finish_step, phase_chord).
+// FP32 products stage each block's gathered vector entries in shared memory (per-block gather lists).
 //
 // Work split. The grid is cut into teams of CTAs; a team processes a fixed list of instances one after the
 // other, all of its CTAs working on the same instance. Rows are grouped in chunks of kBlock * rpt rows
@@ -691,7 +695,7 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
 }
 
 // ------------------------------------------------------------------ multigrid V-cycle (preconditioner)
-// SELL-32 SpMV helpers on one level's arrays.
+// SpMV helpers on one level's arrays (SELL-32: P, and the level-0 operator).
 template <typename R>
 struct LevelVal;
 template <>
@@ -713,7 +717,7 @@ struct LevelVal<double> {
   __device__ static const double *dense(const Inst &I) { return I.amg_dense64; }
 };
 
-// plain y_i = sum_j m_ij v_j over a SELL-32 matrix (prolongation / restriction / FP64 level operators)
+// plain y_i = sum_j m_ij v_j over a SELL-32 matrix (prolongation; the level-0 operator in FP64)
 template <typename R, typename G>
 __device__ inline void sell_plain(const int32_t *sp, const int32_t *sc, const R *sv, const G *v, int row, R &ax,
                                   R &ay, R &az) {
