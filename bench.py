@@ -76,12 +76,25 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def solve_source_hash():
+def code_tokens(src: str) -> str:
+    """C/CUDA source without comments and with whitespace runs collapsed (what the compiler sees; a comment
+    edit does not change the kernel the recorded counters were taken on)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
+def solve_source_hash(read=None):
     import hashlib
     h = hashlib.sha1()
     for f in ("kernels_solve.cu", "internal.h"):
-        with open(os.path.join(ROOT, "paper_2502_10872_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        if read is None:
+            with open(os.path.join(ROOT, "paper_2502_10872_gb300", "csrc", f), encoding="utf-8") as fh:
+                text = fh.read()
+        else:
+            text = read(f)
+        h.update(code_tokens(text).encode())
     return h.hexdigest()
 
 
