@@ -224,8 +224,9 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
 /* Sizes: out[0] vertices, out[1] triangles, out[2] bending stencils, out[3] bytes of device memory the handle
  * holds, out[4] structural nonzeros of the scalar matrix, out[5] stored (SELL-padded) nonzeros, out[6]
  * force contribution slots, out[7] multigrid levels (0 = Jacobi preconditioner), out[8] algorithmic bytes
- * of one FP32 V-cycle (16 B per level-operator nonzero, 8 B per prolongation / restriction nonzero, 200 B
- * per level row, 4 B per entry of the dense coarsest inverse; 0 without multigrid). */
+ * of one FP32 V-cycle (8 B per nonzero of each level operator above the dense level and of each transfer
+ * operator with the smoother folded in, 136 B per level row, 4 B per entry of the dense coarse operator;
+ * 0 without multigrid). */
 int shell_info(shell_handle *h, int64_t out[9]);
 
 int shell_destroy(shell_handle *h);

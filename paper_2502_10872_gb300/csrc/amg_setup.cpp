@@ -6,6 +6,9 @@
 //   aggregates  greedy: a node whose strong neighbours are all free roots an aggregate with them; leftover
 //               nodes join a neighbouring aggregate; the rest form their own
 //   P           (I - omega D^-1 A) P0, P0 the aggregate indicator (near-null space: constants), omega = 4/(3 rho)
+//   Rs, Ps      R (I - omega A D^-1) and its transpose: the damped-Jacobi sweeps of a V(1,1) cycle folded
+//               into the transfers, so that a level's down step (residual and restriction) and its up step
+//               (correction and post-smoothing) each read only vectors the previous step wrote
 //   A_c         P^T A P (Galerkin), repeated until the level is small; the coarsest is inverted densely
 //   dense end   from the first level of at most dense_max rows down, the cycle (started from zero) is a fixed
 //               linear map of that level's right-hand side: stored as a dense matrix, built by applying the
@@ -307,6 +310,12 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
     }
     F.P = P;
     F.R = transpose(P);
+    HostCsr S = F.A;   // I - omega A D^-1
+    for (int i = 0; i < n; ++i)
+      for (int q = S.ptr[i]; q < S.ptr[i + 1]; ++q)
+        S.val[q] = (S.col[q] == i ? 1.0 : 0.0) - F.omega * F.A.val[q] * F.dinv[S.col[q]];
+    F.Rs = multiply(F.R, S);
+    F.Ps = transpose(F.Rs);
     HostCsr Ac = multiply(F.R, multiply(F.A, P));
     H.levels.emplace_back();
     H.levels.back().A = Ac;

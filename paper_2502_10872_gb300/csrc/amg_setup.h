@@ -22,6 +22,11 @@ struct HostAmgLevel {
   HostCsr A;                        // level operator (level 0: the step matrix)
   HostCsr P;                        // prolongation: rows of this level -> columns of the next
   HostCsr R;                        // restriction P^T
+  // The smoother folded into the transfers (what the GPU cycle applies): Rs = R (I - omega A D^-1) maps the
+  // level's right-hand side b to the restricted residual of its pre-smoothing from zero, R (b - A omega
+  // D^-1 b); Ps = Rs^T = (I - omega D^-1 A) P maps the coarse solution to the coarse correction plus the
+  // post-smoothing sweep's response to it.
+  HostCsr Rs, Ps;
   std::vector<double> dinv;         // 1 / diag(A)
   std::vector<double> rowsum;       // sum_j A_ij (FP64)
   double omega = 0.0;               // damped-Jacobi weight 4 / (3 rho(D^-1 A))

@@ -707,9 +707,9 @@ std::vector<double> to_soa(const double *aos, int nv) {
 }
 
 // Multigrid preconditioner: download the assembled FP64 matrix, build the smoothed-aggregation hierarchy
-// on the host (the matrix is constant, so this happens once) and upload its levels: P in SELL-32, R and the
-// coarse operators with 4 lanes per row, the dense operator of the coarse end of the cycle, and (FP32
-// instances) the gather lists of every product.
+// on the host (the matrix is constant, so this happens once) and upload its levels: the transfers with the
+// smoother folded in (Ps in SELL-32, Rs with 4 lanes per row), the coarse operators with 4 lanes per row,
+// the dense operator of the coarse end of the cycle, and (FP32 instances) the gather lists of every product.
 int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   Inst &I = h->h;
   cudaStream_t st = h->mem.st;
@@ -745,24 +745,25 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
   build_amg(A, &H);
   const int L = (int)H.levels.size();
   if (L < 2) return SHELL_OK;
-  // one V(1,1) cycle reads every level operator above the dense level twice, P and R once (8 B per FP32
-  // nonzero with its column), about 200 B per row of level vectors, and the dense operator (or the dense
-  // coarsest inverse) once
+  // one V(1,1) cycle reads every level operator above the dense level, Ps and Rs once (8 B per FP32
+  // nonzero with its column); per row of level vectors (16 B each, AoS float4) the down step reads b, x, the
+  // row sum and writes r, the up step reads x, r, D^-1 and writes y, and the level above writes b and x:
+  // 136 B; the dense operator (or the dense coarsest inverse) once
   const int top = H.dense_level > 0 ? H.dense_level : L - 1;
   h->vcycle_bytes = 0;
   for (int l = 0; l < top; ++l) {
     const HostAmgLevel &V = H.levels[l];
-    h->vcycle_bytes += 16 * (int64_t)V.A.val.size() + 200 * (int64_t)V.A.n;
-    h->vcycle_bytes += 8 * (int64_t)(V.P.val.size() + V.R.val.size());
+    h->vcycle_bytes += 8 * (int64_t)V.A.val.size() + 136 * (int64_t)V.A.n;
+    h->vcycle_bytes += 8 * (int64_t)(V.Ps.val.size() + V.Rs.val.size());
   }
-  h->vcycle_bytes += 200 * (int64_t)H.levels[top].A.n;
+  h->vcycle_bytes += 136 * (int64_t)H.levels[top].A.n;
   h->vcycle_bytes += 4 * (int64_t)(H.dense_level > 0 ? H.dense.size() : H.coarse_inv.size());
   std::vector<HostSell> As(L), Ps(L), Rs(L);
   for (int l = 0; l < L; ++l) {
     if (l > 0) As[l] = to_sell4(H.levels[l].A);
     if (l < L - 1) {
-      Ps[l] = to_sell(H.levels[l].P);
-      Rs[l] = to_sell4(H.levels[l].R);
+      Ps[l] = to_sell(H.levels[l].Ps);
+      Rs[l] = to_sell4(H.levels[l].Rs);
     }
   }
   // gather lists for the FP32 products (level 0 shares the instance's)
@@ -772,8 +773,8 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
     const HostAmgLevel &V = H.levels[l];
     if (l > 0) build_halo(V.A.n, V.A.n, As[l].sl_ptr, As[l].sl_col, V.A.ptr, true, &Ha[l], 4);
     if (l < L - 1) {
-      build_halo(V.P.n, V.P.m, Ps[l].sl_ptr, Ps[l].sl_col, V.P.ptr, false, &Hp[l]);
-      build_halo(V.R.n, V.R.m, Rs[l].sl_ptr, Rs[l].sl_col, V.R.ptr, false, &Hr[l], 4);
+      build_halo(V.Ps.n, V.Ps.m, Ps[l].sl_ptr, Ps[l].sl_col, V.Ps.ptr, false, &Hp[l]);
+      build_halo(V.Rs.n, V.Rs.m, Rs[l].sl_ptr, Rs[l].sl_col, V.Rs.ptr, false, &Hr[l], 4);
     }
   }
   const int nc = H.levels[L - 1].A.n;

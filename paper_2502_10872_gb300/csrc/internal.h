@@ -70,15 +70,15 @@ struct AmgDev {
   float *rs32;                   // row sums (FP64 sum, rounded) for the FP32 difference-form SpMV
   float *dinv32;
   double *dinv64;
-  int32_t *p_ptr, *p_col;
+  int32_t *p_ptr, *p_col;        // Ps = (I - omega D^-1 A) P, SELL-32 (fine rows -> next level's columns)
   float *p_val32;
   double *p_val64;
-  int32_t *r_ptr, *r_col;
+  int32_t *r_ptr, *r_col;        // Rs = R (I - omega A D^-1) = Ps^T, 4 lanes per row
   float *r_val32;
   double *r_val64;
   double omega;                  // damped-Jacobi weight
-  void *b, *x, *r, *y;
-  HaloDev ha, hp, hr;            // gather lists of A, P and R (FP32 products)
+  void *b, *x, *r, *y;           // right-hand side, pre-smoothed x, its residual, cycle output (AoS)
+  HaloDev ha, hp, hr;            // gather lists of A, Ps and Rs (FP32 products)
 };
 
 // Per-instance device descriptor (lives in device memory; every pointer is a device pointer).

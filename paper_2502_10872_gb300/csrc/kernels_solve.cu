@@ -792,40 +792,48 @@ __device__ inline void level_a(const AmgDev &L, const D4 *v, int row, double &ax
 // Row phases of one level, each instantiated with and without shared-memory staging (ST; FP32 only), so
 // that a launch's loop carries only the live values of the path it takes.
 
-// residual of level l: r = b - A x
+// ---- one V(1,1) cycle with the damped-Jacobi sweeps folded into the transfers. A level's down step reads
+// only its right-hand side b (and x = omega D^-1 b, the row-local pre-smoothing from zero, written with b):
+//   r  = b - A x                            residual of the pre-smoothing, kept for the up step
+//   bc = Rs b = R r,  Rs = R (I - omega A D^-1)
+//   xc = omega_c Dc^-1 bc                   pre-smoothing of the next level (when it is smoothed)
+// and its up step reads only x, r and the coarse solution yc:
+//   y  = x + omega D^-1 r + Ps yc,  Ps = (I - omega D^-1 A) P = Rs^T
+// which is the post-smoothing sweep z + omega D^-1 (b - A z) of the corrected z = x + P yc, expanded. So a
+// level costs two team phases instead of four (residual, restriction, correction, post-smoothing).
+
+// residual of one 256-row block of level 0: r = b - A x
 template <typename R, bool ST>
-__device__ void lv_resid(const AmgDev &A, const Team &tm) {
+__device__ __forceinline__ void resid_blk(const AmgDev &A, int blk) {
   typedef typename Vec<R>::G G;
   const G *b = reinterpret_cast<const G *>(A.b);
   const G *x = reinterpret_cast<const G *>(A.x);
   G *rr = reinterpret_cast<G *>(A.r);
-  for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
-    const int row = ch * kBlock + (int)threadIdx.x;
-    R ax, ay, az;
-    if constexpr (ST) {
-      float4 ui;
-      staged_row<true>(A.ha, ch, x, A.a_ptr, A.a_val32, A.rs32, row, row < A.n, ax, ay, az, ui);
-      if (row >= A.n) continue;
-    } else {
-      if (row >= A.n) continue;
-      level_a(A, x, row, ax, ay, az);
-    }
-    const G bi = ldg4(b + row);
-    rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
+  const int row = blk * kBlock + (int)threadIdx.x;
+  R ax, ay, az;
+  if constexpr (ST) {
+    float4 ui;
+    staged_row<true>(A.ha, blk, x, A.a_ptr, A.a_val32, A.rs32, row, row < A.n, ax, ay, az, ui);
+    if (row >= A.n) return;
+  } else {
+    if (row >= A.n) return;
+    level_a(A, x, row, ax, ay, az);
   }
+  const G bi = ldg4(b + row);
+  rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
 }
 
-// restriction to level l+1 with its pre-smoothing from zero fused: bc = R r; xc = omega_c Dc^-1 bc.
-// R has 4 lanes per row (its rows are long): a CTA takes 64 coarse rows, lane k % 4 of a row sums the
-// entries k, k + 4, ... in increasing order, and the four partial sums are added in a fixed shuffle tree;
-// staged (FP32) and unstaged products run the same arithmetic. The loads that do not depend on the staged
-// vector (slice bounds, first nonzeros) are issued before the staging barrier.
+// restriction of one 64-row block of the next level with its pre-smoothing from zero fused: bc = Rs b;
+// xc = omega_c Dc^-1 bc. Rs has 4 lanes per row (its rows are long): lane k % 4 of a row sums the entries
+// k, k + 4, ... in increasing order, and the four partial sums are added in a fixed shuffle tree; staged
+// (FP32) and unstaged products run the same arithmetic. The loads that do not depend on the staged vector
+// (slice bounds, first nonzeros) are issued before the staging barrier.
 template <typename R, bool ST>
-__device__ void lv_restrict(const AmgDev &A, const AmgDev &C, bool pre, const Team &tm) {
+__device__ __forceinline__ void restrict_blk(const AmgDev &A, const AmgDev &C, bool pre, int blk) {
   typedef typename Vec<R>::G G;
   constexpr int U = 8;
   constexpr int kRows = kBlock / 4;   // coarse rows per CTA pass
-  const G *rr = reinterpret_cast<const G *>(A.r);
+  const G *bf = reinterpret_cast<const G *>(A.b);
   G *bc = reinterpret_cast<G *>(C.b);
   G *xc = reinterpret_cast<G *>(C.x);
   const R *dinvc = LevelVal<R>::dinv(C);
@@ -833,72 +841,73 @@ __device__ void lv_restrict(const AmgDev &A, const AmgDev &C, bool pre, const Te
   const R omc = R(C.omega);
   const int n = A.n_next;
   const int lane = threadIdx.x & 31;
-  for (int ch = tm.rank; ch * kRows < n; ch += tm.size) {
-    const int row = ch * kRows + (int)(threadIdx.x >> 2);
-    const bool valid = row < n;
-    int p = 0, b1 = 0;
-    if (valid) {
-      const int s = row >> 3;
-      p = A.r_ptr[s] + lane;
-      b1 = A.r_ptr[s + 1];
-    }
-    int c[U];
-    R a[U];
+  const int row = blk * kRows + (int)(threadIdx.x >> 2);
+  const bool valid = row < n;
+  int p = 0, b1 = 0;
+  if (valid) {
+    const int s = row >> 3;
+    p = A.r_ptr[s] + lane;
+    b1 = A.r_ptr[s + 1];
+  }
+  int c[U];
+  R a[U];
 #pragma unroll
-    for (int j = 0; j < U; ++j) {
-      const int q = p + 32 * j;
-      const bool ok = q < b1;
-      c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
-      a[j] = ok ? val[q] : R(0);
-    }
-    if constexpr (ST) stage_block(A.hr, ch, reinterpret_cast<const float4 *>(rr));
-    R ax = R(0), ay = R(0), az = R(0);
-    if (valid) {
-      for (;;) {
+  for (int j = 0; j < U; ++j) {
+    const int q = p + 32 * j;
+    const bool ok = q < b1;
+    c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
+    a[j] = ok ? val[q] : R(0);
+  }
+  if constexpr (ST) stage_block(A.hr, blk, reinterpret_cast<const float4 *>(bf));
+  R ax = R(0), ay = R(0), az = R(0);
+  if (valid) {
+    for (;;) {
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-          G t;
-          if constexpr (ST)
-            t = sh_halo[c[j]];
-          else
-            t = ldg4(rr + c[j]);
-          ax += a[j] * R(t.x);
-          ay += a[j] * R(t.y);
-          az += a[j] * R(t.z);
-        }
-        p += 32 * U;
-        if (p >= b1) break;
+      for (int j = 0; j < U; ++j) {
+        G t;
+        if constexpr (ST)
+          t = sh_halo[c[j]];
+        else
+          t = ldg4(bf + c[j]);
+        ax += a[j] * R(t.x);
+        ay += a[j] * R(t.y);
+        az += a[j] * R(t.z);
+      }
+      p += 32 * U;
+      if (p >= b1) break;
 #pragma unroll
-        for (int j = 0; j < U; ++j) {
-          const int q = p + 32 * j;
-          const bool ok = q < b1;
-          c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
-          a[j] = ok ? val[q] : R(0);
-        }
+      for (int j = 0; j < U; ++j) {
+        const int q = p + 32 * j;
+        const bool ok = q < b1;
+        c[j] = ok ? (ST ? (int)A.hr.c16[q] : A.r_col[q]) : 0;
+        a[j] = ok ? val[q] : R(0);
       }
     }
-    ax += __shfl_xor_sync(0xffffffffu, ax, 1);
-    ay += __shfl_xor_sync(0xffffffffu, ay, 1);
-    az += __shfl_xor_sync(0xffffffffu, az, 1);
-    ax += __shfl_xor_sync(0xffffffffu, ax, 2);
-    ay += __shfl_xor_sync(0xffffffffu, ay, 2);
-    az += __shfl_xor_sync(0xffffffffu, az, 2);
-    if (valid && (threadIdx.x & 3) == 0) {
-      bc[row] = Vec<R>::mk(ax, ay, az);
-      if (pre) {
-        const R d = omc * dinvc[row];
-        xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
-      }
+  }
+  ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+  ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+  az += __shfl_xor_sync(0xffffffffu, az, 1);
+  ax += __shfl_xor_sync(0xffffffffu, ax, 2);
+  ay += __shfl_xor_sync(0xffffffffu, ay, 2);
+  az += __shfl_xor_sync(0xffffffffu, az, 2);
+  if (valid && (threadIdx.x & 3) == 0) {
+    bc[row] = Vec<R>::mk(ax, ay, az);
+    if (pre) {
+      const R d = omc * dinvc[row];
+      xc[row] = Vec<R>::mk(d * ax, d * ay, d * az);
     }
   }
 }
 
-// coarse correction: x += P yc
+// up step of a level: y = x + omega D^-1 r + Ps yc (256-row blocks, Ps in SELL-32)
 template <typename R, bool ST>
-__device__ void lv_prolong(const AmgDev &A, const AmgDev &C, const Team &tm) {
+__device__ void lv_up(const AmgDev &A, const AmgDev &C, typename Vec<R>::G *y, const Team &tm) {
   typedef typename Vec<R>::G G;
-  G *x = reinterpret_cast<G *>(A.x);
+  const G *x = reinterpret_cast<const G *>(A.x);
+  const G *rr = reinterpret_cast<const G *>(A.r);
   const G *yc = reinterpret_cast<const G *>(C.y);
+  const R *dinv = LevelVal<R>::dinv(A);
+  const R om = R(A.omega);
   for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
     const int row = ch * kBlock + (int)threadIdx.x;
     R ax, ay, az;
@@ -911,33 +920,9 @@ __device__ void lv_prolong(const AmgDev &A, const AmgDev &C, const Team &tm) {
       sell_plain<R, G>(A.p_ptr, A.p_col, LevelVal<R>::p(A), yc, row, ax, ay, az);
     }
     const G xi = ldg4(x + row);
-    x[row] = Vec<R>::mk(R(xi.x) + ax, R(xi.y) + ay, R(xi.z) + az);
-  }
-}
-
-// post-smoothing: y = x + omega D^-1 (b - A x)
-template <typename R, bool ST>
-__device__ void lv_smooth(const AmgDev &A, typename Vec<R>::G *y, const Team &tm) {
-  typedef typename Vec<R>::G G;
-  const G *b = reinterpret_cast<const G *>(A.b);
-  const G *x = reinterpret_cast<const G *>(A.x);
-  const R *dinv = LevelVal<R>::dinv(A);
-  const R om = R(A.omega);
-  for (int ch = tm.rank; ch * kBlock < A.n; ch += tm.size) {
-    const int row = ch * kBlock + (int)threadIdx.x;
-    R ax, ay, az;
-    G xi;
-    if constexpr (ST) {
-      staged_row<true>(A.ha, ch, x, A.a_ptr, A.a_val32, A.rs32, row, row < A.n, ax, ay, az, xi);
-      if (row >= A.n) continue;
-    } else {
-      if (row >= A.n) continue;
-      level_a(A, x, row, ax, ay, az);
-      xi = ldg4(x + row);
-    }
-    const G bi = ldg4(b + row);
+    const G ri = ldg4(rr + row);
     const R d = om * dinv[row];
-    y[row] = Vec<R>::mk(R(xi.x) + d * (R(bi.x) - ax), R(xi.y) + d * (R(bi.y) - ay), R(xi.z) + d * (R(bi.z) - az));
+    y[row] = Vec<R>::mk(R(xi.x) + d * R(ri.x) + ax, R(xi.y) + d * R(ri.y) + ay, R(xi.z) + d * R(ri.z) + az);
   }
 }
 
@@ -1026,28 +1011,26 @@ __device__ __forceinline__ void coarse_row(const AmgDev &A, const typename Vec<R
   }
 }
 
-// residual of a coarse level: r = b - A x
+// residual of one 64-row block of a coarse level: r = b - A x
 template <typename R, bool ST>
-__device__ void lv_resid4(const AmgDev &A, const Team &tm) {
+__device__ __forceinline__ void resid4_blk(const AmgDev &A, int blk) {
   typedef typename Vec<R>::G G;
   const G *b = reinterpret_cast<const G *>(A.b);
   const G *x = reinterpret_cast<const G *>(A.x);
   G *rr = reinterpret_cast<G *>(A.r);
-  for (int ch = tm.rank; ch * (kBlock / 4) < A.n; ch += tm.size) {
-    const int row = ch * (kBlock / 4) + (int)(threadIdx.x >> 2);
-    const bool valid = row < A.n;
-    R ax, ay, az;
-    G ui;
-    coarse_row<R, ST>(A, x, ch, row, valid, ax, ay, az, ui);
-    if (valid && (threadIdx.x & 3) == 0) {
-      const G bi = ldg4(b + row);
-      rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
-    }
+  const int row = blk * (kBlock / 4) + (int)(threadIdx.x >> 2);
+  const bool valid = row < A.n;
+  R ax, ay, az;
+  G ui;
+  coarse_row<R, ST>(A, x, blk, row, valid, ax, ay, az, ui);
+  if (valid && (threadIdx.x & 3) == 0) {
+    const G bi = ldg4(b + row);
+    rr[row] = Vec<R>::mk(R(bi.x) - ax, R(bi.y) - ay, R(bi.z) - az);
   }
 }
 
-// damped-Jacobi sweep of a coarse level: y = x + omega D^-1 (b - A x) (post-smoothing: x is the corrected
-// pre-smoothed vector; coarsest-level sweeps: x the previous sweep)
+// damped-Jacobi sweep of a coarse level: y = x + omega D^-1 (b - A x), x the previous sweep (the coarsest
+// level's sweeps when it is too large for a dense inverse)
 template <typename R, bool ST>
 __device__ void lv_smooth4(const AmgDev &A, const typename Vec<R>::G *x, typename Vec<R>::G *y, const Team &tm) {
   typedef typename Vec<R>::G G;
@@ -1074,35 +1057,39 @@ __device__ inline bool staged(const HaloDev &H, int cap) {
   return sizeof(R) == 4 && halo_on(H, cap);
 }
 
-// One level of the down sweep: residual, then restriction (with the next level's pre-smoothing fused).
+// Down step of level l in one team phase: the residual blocks of level l and the restriction blocks of level
+// l + 1 are independent (both read only b and x), so the team's CTAs take them from one list of units.
 template <typename R>
-__device__ bool down_resid(const Inst &I, int l, const Team &tm) {
-  const AmgDev &A = I.amg[l];
-  const bool st = staged<R>(A.ha, tm.cap);
-  if (l == 0) {
-    if (st)
-      lv_resid<R, (sizeof(R) == 4)>(A, tm);
-    else
-      lv_resid<R, false>(A, tm);
-  } else {
-    if (st)
-      lv_resid4<R, (sizeof(R) == 4)>(A, tm);
-    else
-      lv_resid4<R, false>(A, tm);
-  }
-  return team_sync(tm);
-}
-template <typename R>
-__device__ bool down_restrict(const Inst &I, int l, const Team &tm) {
+__device__ bool down_step(const Inst &I, int l, const Team &tm) {
   const AmgDev &A = I.amg[l];
   const AmgDev &C = I.amg[l + 1];
   // levels at and below the dense level, and the coarsest, are solved, not smoothed
   const int top = I.amg_dense_level > 0 ? I.amg_dense_level : I.amg_levels - 1;
   const bool pre = l + 1 < top;
-  if (staged<R>(A.hr, tm.cap))
-    lv_restrict<R, (sizeof(R) == 4)>(A, C, pre, tm);
-  else
-    lv_restrict<R, false>(A, C, pre, tm);
+  const int fr = l == 0 ? kBlock : kBlock / 4;   // rows per residual block
+  const int nf = (A.n + fr - 1) / fr;
+  const int nu = nf + (A.n_next + kBlock / 4 - 1) / (kBlock / 4);
+  const bool sa = staged<R>(A.ha, tm.cap), sr = staged<R>(A.hr, tm.cap);
+  for (int u = tm.rank; u < nu; u += tm.size) {
+    if (u < nf) {
+      if (l == 0) {
+        if (sa)
+          resid_blk<R, (sizeof(R) == 4)>(A, u);
+        else
+          resid_blk<R, false>(A, u);
+      } else {
+        if (sa)
+          resid4_blk<R, (sizeof(R) == 4)>(A, u);
+        else
+          resid4_blk<R, false>(A, u);
+      }
+    } else {
+      if (sr)
+        restrict_blk<R, (sizeof(R) == 4)>(A, C, pre, u - nf);
+      else
+        restrict_blk<R, false>(A, C, pre, u - nf);
+    }
+  }
   return team_sync(tm);
 }
 
@@ -1153,31 +1140,18 @@ __device__ bool coarsest(const Inst &I, const Team &tm) {
   return true;
 }
 
-// One level of the up sweep: coarse correction and post-smoothing; the output of level 0 is u (in g).
+// Up step of level l in one team phase (coarse correction and post-smoothing); the output of level 0 is u
+// (in g).
 template <typename R>
-__device__ bool up_level(const Inst &I, int l, const Team &tm) {
+__device__ bool up_step(const Inst &I, int l, const Team &tm) {
   typedef typename Vec<R>::G G;
   const AmgDev &A = I.amg[l];
   const AmgDev &C = I.amg[l + 1];
   G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
   if (staged<R>(A.hp, tm.cap))
-    lv_prolong<R, (sizeof(R) == 4)>(A, C, tm);
+    lv_up<R, (sizeof(R) == 4)>(A, C, y, tm);
   else
-    lv_prolong<R, false>(A, C, tm);
-  if (!team_sync(tm)) return false;
-  const bool st = staged<R>(A.ha, tm.cap);
-  const G *x = reinterpret_cast<const G *>(A.x);
-  if (l == 0) {
-    if (st)
-      lv_smooth<R, (sizeof(R) == 4)>(A, y, tm);
-    else
-      lv_smooth<R, false>(A, y, tm);
-  } else {
-    if (st)
-      lv_smooth4<R, (sizeof(R) == 4)>(A, x, y, tm);
-    else
-      lv_smooth4<R, false>(A, x, y, tm);
-  }
+    lv_up<R, false>(A, C, y, tm);
   return team_sync(tm);
 }
 
@@ -1239,20 +1213,20 @@ __device__ bool dense_level(const Inst &I, const Team &tm) {
   return team_sync(tm);
 }
 
-// u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing and Galerkin coarse operators; the part
-// of the cycle from the dense level down is one dense product (else the coarsest level is solved with its
-// dense inverse or Jacobi sweeps); output u in g (AoS). Expects the level-0 pre-smoothing (done by the
-// phase that wrote r) and a team barrier before it.
-// The pre-smoothing of each coarser level is fused into the restriction that produces its right-hand
-// side. Returns false on abort.
+// u = B r: one symmetric V(1,1) cycle with damped-Jacobi smoothing and Galerkin coarse operators, two team
+// phases per level (the sweeps folded into the transfers); the part of the cycle from the dense level down
+// is one dense product (else the coarsest level is solved with its dense inverse or Jacobi sweeps); output
+// u in g (AoS). Expects the level-0 pre-smoothing (done by the phase that wrote r) and a team barrier
+// before it. The pre-smoothing of each coarser level is fused into the restriction that produces its
+// right-hand side. Returns false on abort.
 template <typename R>
 __device__ bool vcycle(const Inst &I, const Team &tm) {
   const int top = I.amg_dense_level > 0 ? I.amg_dense_level : I.amg_levels - 1;
   for (int l = 0; l < top; ++l)
-    if (!down_resid<R>(I, l, tm) || !down_restrict<R>(I, l, tm)) return false;
+    if (!down_step<R>(I, l, tm)) return false;
   if (!(I.amg_dense_level > 0 ? dense_level<R>(I, tm) : coarsest<R>(I, tm))) return false;
   for (int l = top - 1; l >= 0; --l)
-    if (!up_level<R>(I, l, tm)) return false;
+    if (!up_step<R>(I, l, tm)) return false;
   return true;
 }
 
