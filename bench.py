@@ -99,16 +99,17 @@ def solve_source_hash(read=None):
 
 
 def measured_traffic(workload_name):
-    """DRAM bytes per solve launch from the committed ncu summary, if it was taken on the current source of
-    the solve kernel and this workload (else None)."""
+    """(DRAM bytes of one solve launch, algorithmic bytes of that same launch) from the committed ncu summary,
+    if it was taken on the current source of the solve kernel and this workload (else (None, None))."""
     path = os.path.join(ROOT, "profiles", "k_solve_traffic.txt")
     try:
         kv = dict(line.split(None, 1) for line in open(path) if line.strip() and not line.startswith("#"))
     except Exception:
-        return None
+        return None, None
     if kv.get("source_sha1", "").strip() != solve_source_hash() or kv.get("workload", "").strip() != workload_name:
-        return None
-    return float(kv["traffic_bytes_per_launch"])
+        return None, None
+    algo = kv.get("algorithmic_bytes_of_captured_launch")
+    return float(kv["traffic_bytes_per_launch"]), (float(algo) if algo else None)
 
 
 def rank_seed(seed, rank):
@@ -388,6 +389,9 @@ def main():
     solve_s = kern32[1] / 1000.0
     achieved = algo / K / (solve_s / K) / 1e9
     peak, peak_kind = load_peaks()
+    # DRAM traffic of one steady-state launch from a committed ncu capture, with that launch's own
+    # algorithmic bytes (its iteration counts differ a little from the timed steps' mean)
+    traffic, traffic_algo = measured_traffic(args.workload)
     # per step: one FP32 force launch over all instances and one persistent solve launch (per chord iteration)
     lps = int(args.nonlinear.split(",")[0]) if args.nonlinear else 1
     lps = max(1, lps)
@@ -470,7 +474,8 @@ def main():
                    "max_inner_iterations_per_step": float(np.max(iters)),
                    "mean_refine_rounds_per_step": float(np.mean(rounds))},
         "roofline": {"kernel": "k_solve", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(args.workload), "peak_kind": peak_kind,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_launch_algorithmic_bytes": traffic_algo,
+                     "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo / (K * lps), "mean_launch_ms": kern32[1] / (K * lps),
                      "force_kernel_ms_per_step": kern32[0] / K},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),
