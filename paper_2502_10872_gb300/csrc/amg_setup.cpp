@@ -310,13 +310,34 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
     }
     F.P = P;
     F.R = transpose(P);
-    HostCsr S = F.A;   // I - omega A D^-1
-    for (int i = 0; i < n; ++i)
-      for (int q = S.ptr[i]; q < S.ptr[i + 1]; ++q)
-        S.val[q] = (S.col[q] == i ? 1.0 : 0.0) - F.omega * F.A.val[q] * F.dinv[S.col[q]];
-    F.Rs = multiply(F.R, S);
-    F.Ps = transpose(F.Rs);
-    HostCsr Ac = multiply(F.R, multiply(F.A, P));
+    const HostCsr AP = multiply(F.A, P);
+    // Ps = P - omega D^-1 (A P), merged row by row (both rows sorted by column), and Rs = Ps^T
+    HostCsr &Ps = F.Ps;
+    Ps.n = n;
+    Ps.m = na;
+    Ps.ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      int q = P.ptr[i];
+      const int q1 = P.ptr[i + 1];
+      const double s = -F.omega * F.dinv[i];
+      for (int k = AP.ptr[i]; k < AP.ptr[i + 1]; ++k) {
+        for (; q < q1 && P.col[q] < AP.col[k]; ++q) {
+          Ps.col.push_back(P.col[q]);
+          Ps.val.push_back(P.val[q]);
+        }
+        double v = s * AP.val[k];
+        if (q < q1 && P.col[q] == AP.col[k]) v += P.val[q++];
+        Ps.col.push_back(AP.col[k]);
+        Ps.val.push_back(v);
+      }
+      for (; q < q1; ++q) {
+        Ps.col.push_back(P.col[q]);
+        Ps.val.push_back(P.val[q]);
+      }
+      Ps.ptr[i + 1] = (int32_t)Ps.col.size();
+    }
+    F.Rs = transpose(Ps);
+    HostCsr Ac = multiply(F.R, AP);
     H.levels.emplace_back();
     H.levels.back().A = Ac;
     finish_level(H.levels.back());
