@@ -211,10 +211,10 @@ int shell_forces(shell_handle *h, double *out_xyz);
 int shell_apply_matrix(shell_handle *h, const double *in_xyz, double *out_xyz);
 
 /* Copy the state to / from host buffers [V][3] (either pointer may be NULL to skip it). Each step's solver
- * starts from the velocity extrapolated quadratically from the last three committed steps
- * (3 (v - v_prev) + v_prev2); setting a state keeps v_prev and v_prev2, since they only shape the initial
- * guess (results agree to the solve tolerance either way, and writing back an unchanged state leaves the
- * next step bitwise unchanged). */
+ * starts from the velocity extrapolated cubically from the last four committed steps
+ * (4 (v + v_prev2) - 6 v_prev - v_prev3); setting a state keeps the three earlier velocities, since they
+ * only shape the initial guess (results agree to the solve tolerance either way, and writing back an
+ * unchanged state leaves the next step bitwise unchanged). */
 int shell_get_state(shell_handle *h, double *x, double *v);
 int shell_set_state(shell_handle *h, const double *x, const double *v);
 

@@ -1020,6 +1020,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.v = C.take<double>(3 * (size_t)nv);
     I.vprev = C.take<double>(3 * (size_t)nv);
     I.vprev2 = C.take<double>(3 * (size_t)nv);
+    I.vprev3 = C.take<double>(3 * (size_t)nv);
     I.xk = C.take<double>(3 * (size_t)nv);
     I.rest = C.take<double>(3 * (size_t)nv);
     I.fext = C.take<double>(3 * (size_t)nv);
@@ -1150,6 +1151,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   CKF(up(I.v, v0.data(), 8 * v0.size()));
   CKF(up(I.vprev, v0.data(), 8 * v0.size()));
   CKF(up(I.vprev2, v0.data(), 8 * v0.size()));
+  CKF(up(I.vprev3, v0.data(), 8 * v0.size()));
   CKF(up(I.pinned, pin.data(), nv));
   CKF(up(I.t_idx, T.t_idx.data(), 4 * T.t_idx.size()));
   CKF(up(I.t_bc, T.t_bc.data(), T.t_bc.size()));

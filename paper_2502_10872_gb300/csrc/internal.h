@@ -100,7 +100,7 @@ struct Inst {
   // state (FP64, SoA [3][nv])
   double *x, *v, *rest, *fext;
   double *vprev;                 // velocity before the last committed step (warm-start extrapolation)
-  double *vprev2;                // velocity before the one before (quadratic extrapolation)
+  double *vprev2, *vprev3;       // the two velocities before that (cubic extrapolation)
   double *xk;                    // [3][nv] chord iterate x + dt v_k, where the next forces are evaluated
   double *mass;                  // [nv]
   uint8_t *pinned;               // [nv]

@@ -491,8 +491,8 @@ __device__ __forceinline__ void staged_row64(const HaloDev &H, int blk, const D4
   }              \
   }
 
-// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = 3 (v - v_prev) + v_prev2; g64 = sol;
-// partial ||b||^2
+// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = 4 (v + v_prev2) - 6 v_prev - v_prev3;
+// g64 = sol; partial ||b||^2
 // Chord iteration k > 0 of the exact backward-Euler step (forces at x + dt v_k, v_k in sol and g64):
 // b = M v + dt (f + f_ext) + (A - M) v_k, warm start v_k kept, so that the first residual b - A v_k is
 // -R(v_k), the backward-Euler residual, and the solve gives v_{k+1} = v_k - A^-1 R(v_k).
@@ -526,11 +526,12 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
         if (pin) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
-        // initial guess: quadratic extrapolation of the last three velocities, 3 (v - v_prev) + v_prev2
-        // (v_prev, v_prev2: the velocities before the last two committed steps; setting a state leaves
-        // them, as they only shape the initial guess)
+        // initial guess: cubic extrapolation of the last four velocities, 4 (v + v_prev2) - 6 v_prev - v_prev3
+        // (v_prev, v_prev2, v_prev3: the velocities before the last three committed steps; setting a state
+        // leaves them, as they only shape the initial guess)
         if (!chord) {
-          sv[c] = pin ? 0.0 : 3.0 * (v - I.vprev[c * nv + row]) + I.vprev2[c * nv + row];
+          const int k = c * nv + row;
+          sv[c] = pin ? 0.0 : 4.0 * (v + I.vprev2[k]) - 6.0 * I.vprev[k] - I.vprev3[k];
           I.sol[c * nv + row] = sv[c];
         }
       }
@@ -1285,13 +1286,14 @@ __device__ void phase_accumulate(const Inst &I, const Team &tm) {
   ROWS_END
 }
 
-// v_prev2 = v_prev; v_prev = v; v = sol; x += dt v
+// v_prev3 = v_prev2; v_prev2 = v_prev; v_prev = v; v = sol; x += dt v
 __device__ void phase_commit(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   ROWS_BEGIN(I, tm)
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
     const double v = I.sol[k];
+    I.vprev3[k] = I.vprev2[k];
     I.vprev2[k] = I.vprev[k];
     I.vprev[k] = I.v[k];
     I.v[k] = v;
