@@ -122,7 +122,7 @@ typedef struct shell_options {
   double dt;               /* time step > 0 */
   int32_t precision;       /* shell_precision */
   double pcg_rtol;         /* stop when ||r|| <= pcg_rtol ||b|| (FP64); inner relative tolerance (FP32; a
-                            * round also stops once its residual is 0.3 refine_rtol ||b||) */
+                            * round also stops once its residual is 0.7 refine_rtol ||b||) */
   double refine_rtol;      /* FP32_REFINE: stop when the FP64 residual ||b - A v|| <= refine_rtol ||b|| */
   int32_t pcg_max_it;      /* iteration cap per solve (per inner solve in FP32_REFINE) */
   int32_t refine_max;      /* FP32_REFINE: cap on refinement rounds */

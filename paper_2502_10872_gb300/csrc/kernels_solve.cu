@@ -1473,9 +1473,10 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
         set_status(I, tm, SHELL_ERR_NOT_CONVERGED, total, rounds, rel);
         return true;
       }
-      // inner target: the relative reduction pcg_rtol, but no further than a margin below the refinement
-      // target (a round that starts close to it needs only a few iterations), and at least a halving
-      const double tol2 = fmin(fmax(tin2 * r2, 0.09 * tol_ref2), 0.25 * r2);
+      // inner target: the relative reduction pcg_rtol, but no further than 0.7 of the refinement target (a
+      // round that starts close to it needs only a few iterations; the FP64 test above decides, and a
+      // margin of 0.7 leaves room for the FP32 recurrence's drift), and at least a halving
+      const double tol2 = fmin(fmax(tin2 * r2, 0.5 * tol_ref2), 0.25 * r2);
       double rho = 0.0;
       const int it = cg_loop<float>(I, tm, reinterpret_cast<float *>(I.xs), tol2, I.pcg_max_it, &rho);
       if (it == -2) return false;
