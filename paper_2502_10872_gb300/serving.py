@@ -1,8 +1,9 @@
 """Continuous-batching request loop over the C-ABI batch (argument marshalling and scheduling only).
 
 Requests (meshes with a step count) arrive over time. A request is admitted as soon as the batch's HBM
-budget holds its instance: its handle is created (host topology plus the GPU precompute and assembly) on a
-worker thread while the GPU steps the resident instances, then it joins the batch between two steps. Every
+budget holds its instance: its handle is created (host topology, multigrid set-up, the GPU precompute and
+assembly) on one of a few worker threads while the GPU steps the resident instances, then it joins the
+batch between two steps. Set-up is mostly host work, so several requests are built at once. Every
 step advances all resident instances in one force launch and one persistent solve launch. A request retires
 (and frees its device memory) after its last step. Each instance's result does not depend on the others
 in the batch (deterministic, team-size independent reductions), so a request gives the same state alone or
@@ -73,8 +74,17 @@ class Server:
     """Admit requests into one batch by an HBM budget and step them together."""
 
     def __init__(self, budget_bytes: int, precision: str = "fp32_refine", keep_states: bool = False,
-                 create_kw: Optional[dict] = None, clock: Callable[[], float] = time.perf_counter):
+                 create_kw: Optional[dict] = None, clock: Callable[[], float] = time.perf_counter,
+                 n_workers: int = 4):
         self.budget = int(budget_bytes)
+        self.n_workers = max(1, int(n_workers))
+        self.device = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                self.device = torch.cuda.current_device()
+        except Exception:
+            pass
         self.precision = precision
         self.keep_states = keep_states
         self.create_kw = create_kw or {}
@@ -83,6 +93,9 @@ class Server:
         self.used = 0
 
     def _create(self, req: Request):
+        if self.device is not None:   # the CUDA device is per thread
+            import torch
+            torch.cuda.set_device(self.device)
         req.handle = gb.create_from_scenario(req.scenario, precision=self.precision, **self.create_kw)
 
     def run(self, requests: List[Request], max_wall_s: float = 1e9, steps_per_launch: int = 1) -> ServeReport:
@@ -93,24 +106,30 @@ class Server:
         vsteps = 0
         nsteps = 0
         t0 = self.clock()
-        worker: Optional[threading.Thread] = None
-        building: Optional[Request] = None
+        building: list = []             # (thread, request) being created
 
         def now():
             return self.clock() - t0
 
-        while pending or ready or active or building is not None:
+        while pending or ready or active or building:
             if now() > max_wall_s:
                 break
-            # start building the next arrived request on the worker thread (overlaps the GPU step)
-            if worker is None and pending and pending[0].arrival_s <= now():
-                building = pending.popleft()
-                worker = threading.Thread(target=self._create, args=(building,))
-                worker.start()
-            if worker is not None and not worker.is_alive():
-                worker.join()
-                ready.append(building)
-                worker, building = None, None
+            # start building arrived requests on worker threads (overlaps the GPU step)
+            while len(building) < self.n_workers and pending and pending[0].arrival_s <= now():
+                req = pending.popleft()
+                th = threading.Thread(target=self._create, args=(req,))
+                th.start()
+                building.append((th, req))
+            still = []
+            for th, req in building:
+                if th.is_alive():
+                    still.append((th, req))
+                else:
+                    th.join()
+                    if req.handle is None:
+                        raise RuntimeError(f"request {req.rid}: shell_create failed on its worker thread")
+                    ready.append(req)
+            building = still
             # admit what fits the budget
             while ready:
                 req = ready[0]
@@ -124,8 +143,8 @@ class Server:
                 active[req.slot] = req
                 ready.popleft()
             if not active:
-                if worker is not None:
-                    worker.join(timeout=0.001)
+                if building:
+                    building[0][0].join(timeout=0.001)
                 elif pending:
                     time.sleep(min(0.001, max(0.0, pending[0].arrival_s - now())))
                 continue
@@ -151,8 +170,11 @@ class Server:
                     req.handle = None
                     del active[slot]
         wall = now()
-        if worker is not None:
-            worker.join()
+        for th, req in building:
+            th.join()
+            if req.handle is not None:   # built after the wall limit: never admitted
+                gb.shell_destroy(req.handle)
+                req.handle = None
         return ServeReport(wall, vsteps, nsteps, np.asarray(lat, np.float64), list(requests))
 
     def close(self):
