@@ -1,5 +1,6 @@
 // api.cpp -- the C ABI (include/shell.h): handles, batches, device memory, launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -183,27 +184,39 @@ struct shell_batch {
 
 namespace {
 
+// Device properties queried once (atomics: handles may be created on several threads; racing threads
+// compute the same value).
 // CTAs per SM of the solve variant compiled for `occ` (FP32: variants for 3, 4, 5; others one variant)
 int blocks_per_sm_cached(int prec, int occ = 3) {
-  static int n[3][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  static std::atomic<int> n[3][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
   occ = std::max(1, std::min(5, occ));
-  if (n[prec][occ] < 0) n[prec][occ] = std::max(1, solve_blocks_per_sm(prec, occ));
-  return n[prec][occ];
+  int v = n[prec][occ].load();
+  if (v < 0) {
+    v = std::max(1, solve_blocks_per_sm(prec, occ));
+    n[prec][occ].store(v);
+  }
+  return v;
 }
 int max_occ(int prec) { return prec == 2 ? blocks_per_sm_cached(2, 5) : blocks_per_sm_cached(prec, 2); }
 int max_clusters_cached(int prec) {
-  static int n[3] = {-1, -1, -1};
-  if (n[prec] < 0) n[prec] = std::max(0, solve_max_clusters(prec, kCluster));
-  return n[prec];
+  static std::atomic<int> n[3] = {-1, -1, -1};
+  int v = n[prec].load();
+  if (v < 0) {
+    v = std::max(0, solve_max_clusters(prec, kCluster));
+    n[prec].store(v);
+  }
+  return v;
 }
 int num_sms() {
-  static int n = -1;
-  if (n < 0) {
+  static std::atomic<int> n{-1};
+  int v = n.load();
+  if (v < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    n.store(v);
   }
-  return n;
+  return v;
 }
 
 void destroy_graph(shell_batch *b) {
