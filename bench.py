@@ -200,19 +200,24 @@ class Clocks:
 def algorithmic_bytes(info, stats, steps):
     """Compulsory DRAM bytes of the solve kernel (FP32 + refinement) for ``steps`` steps of one instance.
 
-    Per step: right-hand side 16 B per contribution slot (FP32 force + its index) + 141 B per row, commit 96 B
-    per row. Per refinement round: FP64 matrix 12 B per nonzero + 216 B per row (FP64 residual, vector
-    gather, inner-solve set-up, correction accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero
-    + 168 B per row (update of r, p, s, x and the gathered vector; w = A u; one gather per row), plus one
-    multigrid V-cycle per iteration and per round when the instance uses the multigrid preconditioner
-    (``vcycle_bytes`` from shell_info). Structural nonzeros are used (SELL padding is overhead). Exact
-    backward Euler: the per-step part once per chord solve, plus the FP64 product (A - M) v_k in the
-    right-hand side of every later solve (12 B per nonzero + 32 B per row).
+    Per step: right-hand side 16 B per contribution slot (FP32 force + its index) + 213 B per row (reads:
+    incidence pointer 4, pinned 1, mass 8, v, f_ext and the three earlier velocities of the warm start 5 x 24;
+    writes: b, the initial guess and its AoS copy 24 + 24 + 32), commit 240 B per row (reads the solution,
+    v, v_prev, v_prev2, x; writes v_prev3, v_prev2, v_prev, v, x; 24 B each). Per refinement round: FP64
+    matrix 12 B per nonzero + 216 B per row (FP64 residual, vector gather, inner-solve set-up, correction
+    accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero + 168 B per row (update of r, p, s, x
+    and the gathered vector; w = A u; one gather per row), plus one multigrid V-cycle per iteration and per
+    round when the instance uses the multigrid preconditioner (``vcycle_bytes`` from shell_info). Structural
+    nonzeros are used (SELL padding is overhead). Exact backward Euler, per later chord solve: the forces'
+    slots again, its right-hand side (v, f_ext, the iterate, pinned, mass, pointer; writes b: 109 B per
+    row) with the FP64 product (A - M) v_k (12 B per nonzero + 32 B per row), and the hand-off to the next
+    iterate (reads x and the solution, writes the iterate positions and the AoS copy: 104 B per row).
     """
     V, nnz, slots = info["n_verts"], info["nnz"], info["n_slots"]
     vc = float(info.get("vcycle_bytes", 0))
     solves = max(1, int(stats.get("nl_iterations", 0)))
-    per_step = solves * (16.0 * slots + (141.0 + 96.0) * V) + (solves - 1) * (12.0 * nnz + 32.0 * V)
+    per_step = (solves * 16.0 * slots + (213.0 + 240.0) * V
+                + (solves - 1) * (12.0 * nnz + (32.0 + 109.0 + 104.0) * V))
     per_round = 12.0 * nnz + 216.0 * V + vc
     per_iter = 8.0 * nnz + 168.0 * V + vc
     return steps * per_step + stats["total_refine_rounds"] * per_round + stats["total_pcg_iterations"] * per_iter
