@@ -303,10 +303,11 @@ __device__ void edge_stencil(const Inst &I, const Data<R> &D, int e, bool want_e
 // chord_k > 0: a later chord iteration of the exact backward-Euler step; only instances whose step is in a
 // chord iteration take part, with forces at their iterate positions xk. The FP32 kernel is held to 64
 // registers (8 blocks per SM): 32 instead of 24 resident warps hide more of each thread's dependent chain
-// (0.245 -> 0.220 ms per batch256 step, 40 bytes of spills); the FP64 one would spill heavily and keeps its own.
+// (0.245 -> 0.220 ms per batch256 step, 40 bytes of spills); the FP64 one would spill heavily and keeps
+// its own.
 template <typename R>
-__global__ void __launch_bounds__(kForceBlock, sizeof(R) == 4 ? 8 : 1) k_forces(const Inst *__restrict__ insts, const Tile *__restrict__ tiles,
-                                                        int want_energy, int chord_k) {
+__global__ void __launch_bounds__(kForceBlock, sizeof(R) == 4 ? 8 : 1)
+    k_forces(const Inst *__restrict__ insts, const Tile *__restrict__ tiles, int want_energy, int chord_k) {
   const Tile tl = tiles[blockIdx.x];
   const Inst &I = insts[tl.inst];
   if (!want_energy && I.status->err != SHELL_OK) return;
