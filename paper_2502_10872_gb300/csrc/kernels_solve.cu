@@ -1,6 +1,7 @@
 // kernels_solve.cu -- persistent per-step solve: right-hand side, preconditioned conjugate gradients on the
-// constant matrix (Jacobi, or a smoothed-aggregation multigrid V-cycle whose coarse end is one dense
-// operator), state update. One launch per step serves every instance of a batch.
+// constant matrix (Jacobi, or a smoothed-aggregation multigrid V-cycle with its damped-Jacobi sweeps folded
+// into the transfers and one dense operator for its coarse end), state update. One launch per step serves
+// every instance of a batch.
 //
 // Step (Section 5, Eq. 62-63, linearised): (M + dt^2 K) v' = M v + dt (f + f_ext); x' = x + dt v'.
 // Exact backward Euler (optional, per instance): the same launch repeated as a chord iteration, each with
@@ -19,10 +20,12 @@
 // order and tree. An instance therefore gets bit-identical results whether it runs alone or in a batch.
 //
 // Solver: Chronopoulos-Gear form of preconditioned CG (one fused reduction of (r,u), (w,u), (r,r) per
-// iteration; two team barriers per iteration):
+// iteration; two team barriers per iteration with the Jacobi preconditioner, and the multigrid cycle adds two
+// per level above its dense end and one for that end):
 //   p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; u = D^-1 r; w = A u;
 //   gamma' = (r,u); delta' = (w,u); beta' = gamma'/gamma; alpha' = gamma'/(delta' - beta' gamma'/alpha).
-// FP64 mode: one CG in FP64 from the warm start v, until ||r|| <= rtol ||b||.
+// Warm start: the velocity extrapolated from the last four (cubic). FP64 mode: one CG in FP64 from it, until
+// ||r|| <= rtol ||b||.
 // FP32 refinement mode: r64 = b - A v in FP64 (FP64 matrix and vector); inner CG in FP32 on A d = r64 from
 // d = 0 to a relative tolerance (or to a margin below the refinement target, if that is reached first);
 // v += d; repeat until ||r64|| <= refine_rtol ||b||.
@@ -698,7 +701,7 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
 }
 
 // ------------------------------------------------------------------ multigrid V-cycle (preconditioner)
-// SpMV helpers on one level's arrays (SELL-32: P, and the level-0 operator).
+// SpMV helpers on one level's arrays (SELL-32: the folded prolongation Ps, and the level-0 operator).
 template <typename R>
 struct LevelVal;
 template <>
@@ -720,7 +723,7 @@ struct LevelVal<double> {
   __device__ static const double *dense(const Inst &I) { return I.amg_dense64; }
 };
 
-// plain y_i = sum_j m_ij v_j over a SELL-32 matrix (prolongation; the level-0 operator in FP64)
+// plain y_i = sum_j m_ij v_j over a SELL-32 matrix (the folded prolongation Ps; the level-0 operator in FP64)
 template <typename R, typename G>
 __device__ inline void sell_plain(const int32_t *sp, const int32_t *sc, const R *sv, const G *v, int row, R &ax,
                                   R &ay, R &az) {
