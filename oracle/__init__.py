@@ -18,7 +18,8 @@ Layout:
 * :mod:`oracle.energies`  -- per-stencil bending energies and exact gradients for the six models
   (Eq. 16-26, Eq. 39-45, Eq. 52-57, App. B) and the corotated constant-strain membrane.
 * :mod:`oracle.system`    -- lumped mass, the constant matrix M + dt^2 (K_b + K_m), the linearised
-  backward-Euler step (Section 5, Eq. 62-63) and energy totals.
+  backward-Euler step (Section 5, Eq. 62-63), the exact backward-Euler step by chord iteration with its
+  residual and incremental potential, and energy totals.
 
 Readings of points the paper leaves open are listed in the docstrings where they are used; the same
 readings are implemented (independently) by the CUDA library.
