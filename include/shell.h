@@ -137,7 +137,7 @@ typedef struct shell_options {
 } shell_options;
 
 /* Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
- * FP64 PCG, 1e-4 for the inner FP32 PCG, 1e-8 for the refinement: the FP32 force rounding, not the
+ * FP64 PCG, 1e-6 for the inner FP32 PCG, 1e-8 for the refinement: the FP32 force rounding, not the
  * solve, then bounds the error), pcg_max_it 20000, refine_max 20,
  * preconditioner AUTO. */
 void shell_default_options(shell_options *opt);

@@ -675,7 +675,7 @@ void batch_free(shell_batch *b) {
 }
 
 void fill_default_tolerances(shell_options *o) {
-  if (!(o->pcg_rtol > 0.0)) o->pcg_rtol = (o->precision == SHELL_FP64) ? 1e-13 : 1e-4;
+  if (!(o->pcg_rtol > 0.0)) o->pcg_rtol = (o->precision == SHELL_FP64) ? 1e-13 : 1e-6;
   if (!(o->refine_rtol > 0.0)) o->refine_rtol = 1e-8;
   if (o->pcg_max_it <= 0) o->pcg_max_it = 20000;
   if (o->refine_max <= 0) o->refine_max = 20;
@@ -920,7 +920,7 @@ void shell_default_options(shell_options *o) {
   std::memset(o, 0, sizeof(*o));
   o->dt = 1e-2;
   o->precision = SHELL_FP64;
-  o->pcg_rtol = 0.0;      // precision default: 1e-13 (FP64) / 1e-4 (FP32 inner)
+  o->pcg_rtol = 0.0;      // precision default: 1e-13 (FP64) / 1e-6 (FP32 inner)
   o->refine_rtol = 0.0;   // 1e-8
   o->pcg_max_it = 20000;
   o->refine_max = 20;

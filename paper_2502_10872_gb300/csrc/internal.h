@@ -149,7 +149,7 @@ struct Inst {
   double *r64;                   // [3][nv] FP64 residual (refinement)
   double *g64;                   // [nv][4] FP64 gathered vector
   void *r, *p, *s, *w;           // [3][nv] PCG vectors in the solve precision
-  void *xs;                      // [3][nv] inner solution (FP32 refinement correction)
+  void *xs;                      // [3][nv] FP64 inner solution (the FP32 refinement round's correction)
   void *g;                       // [nv][4] gathered vector in the solve precision
   double *part;                  // [n_chunks][4] reduction partials
   double *ebuf;                  // [nt + ne][2] per-stencil energies (bending, membrane)

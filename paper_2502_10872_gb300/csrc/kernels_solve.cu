@@ -546,7 +546,7 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
 }
 
 // FP64 residual r64 = b - A64 sol; returns partial ||r64||^2. If R is float also prepares the inner CG:
-// r32 = r64, xs = 0, g32 = D32^-1 r32. If R is double: r = r64 (in place), sol unchanged, g = D^-1 r.
+// r32 = r64, xs = 0 (FP64), g32 = D32^-1 r32. If R is double: r = r64 (in place), sol unchanged, g = D^-1 r.
 // Multigrid: also the first V-cycle's level-0 pre-smoothing from zero, b0 = r, x0 = omega D^-1 r (row-local).
 template <typename R>
 __device__ void phase_resid(const Inst &I, const Team &tm) {
@@ -557,7 +557,7 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
   const R om0 = amg ? R(I.amg[0].omega) : R(0);
   const D4 *g64 = reinterpret_cast<const D4 *>(I.g64);
   R *r = reinterpret_cast<R *>(I.r);
-  R *xs = reinterpret_cast<R *>(I.xs);
+  double *xs = reinterpret_cast<double *>(I.xs);
   typename Vec<R>::G *g = Vec<R>::g(I);
   const R *dinv = Vec<R>::dinv(I);
   const bool st = I.h0.max > 0 && 2 * I.h0.max <= tm.cap;   // FP64 entries take two buffer slots
@@ -586,9 +586,9 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
       r[nv + row] = q1;
       r[2 * nv + row] = q2;
       if (sizeof(R) == 4) {
-        xs[row] = R(0);
-        xs[nv + row] = R(0);
-        xs[2 * nv + row] = R(0);
+        xs[row] = 0.0;
+        xs[nv + row] = 0.0;
+        xs[2 * nv + row] = 0.0;
       }
       const R di = dinv[row];
       g[row] = Vec<R>::mk(di * q0, di * q1, di * q2);
@@ -651,8 +651,11 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
 
 // p = u + beta p; s = w + beta s; x += alpha p; r -= alpha s; then (Jacobi) u = D^-1 r -> g. With the
 // multigrid preconditioner u is read from g and the new u = B r is computed by the V-cycle afterwards.
+// The solution x is accumulated in FP64 in both precisions (alpha_x: alpha in FP64): the recurrences never
+// read it, and in FP32 its rounding alone would leave the refinement's true residual above 1e-8 of ||b||.
 template <typename R>
-__device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, bool first, R *x) {
+__device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, bool first, double *x,
+                             double alpha_x) {
   const int nv = I.nv;
   const bool amg = I.amg_levels > 0;
   const R *dinv = Vec<R>::dinv(I);
@@ -685,7 +688,7 @@ __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, boo
     const R sc = first ? w[k] : w[k] + beta * s[k];
     p[k] = pc;
     s[k] = sc;
-    x[k] += alpha * pc;
+    x[k] += alpha_x * double(pc);
     const R rn = rc - alpha * sc;
     r[k] = rn;
     rv[c] = rn;
@@ -1240,7 +1243,7 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
 // g = D^-1 r. Stops when (r,r) <= tol2 (absolute). Returns iterations (>= 0), -1 on cap, -2 on abort,
 // -3 on a non-finite reduction.
 template <typename R>
-__device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, double *rho_out) {
+__device__ int cg_loop(const Inst &I, Team &tm, double *x, double tol2, int max_it, double *rho_out) {
   if (!team_sync(tm)) return -2;
   if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
   phase_spmv<R>(I, tm);
@@ -1254,7 +1257,7 @@ __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, d
   double alpha = gamma / delta, beta = 0.0;
   bool first = true;
   for (int it = 1; it <= max_it; ++it) {
-    phase_update<R>(I, tm, R(alpha), R(beta), first, x);
+    phase_update<R>(I, tm, R(alpha), R(beta), first, x, alpha);
     if (!team_sync(tm)) return -2;
     if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
     phase_spmv<R>(I, tm);
@@ -1274,15 +1277,15 @@ __device__ int cg_loop(const Inst &I, Team &tm, R *x, double tol2, int max_it, d
   return -1;
 }
 
-// sol += xs (FP32 correction); g64 = sol
+// sol += xs (the inner correction, accumulated in FP64); g64 = sol
 __device__ void phase_accumulate(const Inst &I, const Team &tm) {
   const int nv = I.nv;
-  const float *xs = reinterpret_cast<const float *>(I.xs);
+  const double *xs = reinterpret_cast<const double *>(I.xs);
   ROWS_BEGIN(I, tm)
   double sv[3];
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
-    sv[c] = I.sol[k] + double(xs[k]);
+    sv[c] = I.sol[k] + xs[k];
     I.sol[k] = sv[c];
   }
   reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
@@ -1481,7 +1484,7 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
       // margin of 0.7 leaves room for the FP32 recurrence's drift), and at least a halving
       const double tol2 = fmin(fmax(tin2 * r2, 0.5 * tol_ref2), 0.25 * r2);
       double rho = 0.0;
-      const int it = cg_loop<float>(I, tm, reinterpret_cast<float *>(I.xs), tol2, I.pcg_max_it, &rho);
+      const int it = cg_loop<float>(I, tm, reinterpret_cast<double *>(I.xs), tol2, I.pcg_max_it, &rho);
       if (it == -2) return false;
       if (it == -3) {
         set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
