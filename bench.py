@@ -204,9 +204,10 @@ def algorithmic_bytes(info, stats, steps):
     incidence pointer 4, pinned 1, mass 8, v, f_ext and the three earlier velocities of the warm start 5 x 24;
     writes: b, the initial guess and its AoS copy 24 + 24 + 32), commit 240 B per row (reads the solution,
     v, v_prev, v_prev2, x; writes v_prev3, v_prev2, v_prev, v, x; 24 B each). Per refinement round: FP64
-    matrix 12 B per nonzero + 216 B per row (FP64 residual, vector gather, inner-solve set-up, correction
-    accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero + 168 B per row (update of r, p, s, x
-    and the gathered vector; w = A u; one gather per row), plus one multigrid V-cycle per iteration and per
+    matrix 12 B per nonzero + 240 B per row (FP64 residual, vector gather, inner-solve set-up with the FP64
+    correction zeroed, correction accumulate). Per inner PCG iteration: FP32 matrix 8 B per nonzero + 192 B
+    per row (update of r, p, s, the FP64 correction x and the gathered vector; w = A u; one gather per
+    row), plus one multigrid V-cycle per iteration and per
     round when the instance uses the multigrid preconditioner (``vcycle_bytes`` from shell_info). Structural
     nonzeros are used (SELL padding is overhead). Exact backward Euler, per later chord solve: the forces'
     slots again, its right-hand side (v, f_ext, the iterate, pinned, mass, pointer; writes b: 109 B per
@@ -218,8 +219,8 @@ def algorithmic_bytes(info, stats, steps):
     solves = max(1, int(stats.get("nl_iterations", 0)))
     per_step = (solves * 16.0 * slots + (213.0 + 240.0) * V
                 + (solves - 1) * (12.0 * nnz + (32.0 + 109.0 + 104.0) * V))
-    per_round = 12.0 * nnz + 216.0 * V + vc
-    per_iter = 8.0 * nnz + 168.0 * V + vc
+    per_round = 12.0 * nnz + 240.0 * V + vc
+    per_iter = 8.0 * nnz + 192.0 * V + vc
     return steps * per_step + stats["total_refine_rounds"] * per_round + stats["total_pcg_iterations"] * per_iter
 
 

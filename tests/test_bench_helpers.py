@@ -32,8 +32,8 @@ def test_algorithmic_bytes_terms():
     info = {"n_verts": 1000, "nnz": 19000, "n_slots": 6000, "vcycle_bytes": 5e5}
     stats = {"total_refine_rounds": 3, "total_pcg_iterations": 20}
     per_step = 16 * 6000 + (213 + 240) * 1000
-    per_round = 12 * 19000 + 216 * 1000 + 5e5
-    per_iter = 8 * 19000 + 168 * 1000 + 5e5
+    per_round = 12 * 19000 + 240 * 1000 + 5e5
+    per_iter = 8 * 19000 + 192 * 1000 + 5e5
     assert bench.algorithmic_bytes(info, stats, 2) == 2 * per_step + 3 * per_round + 20 * per_iter
     # exact backward Euler, three chord solves in the step: the slots twice more, and per later solve the
     # product (A - M) v_k, its right-hand side and the hand-off to the next iterate
