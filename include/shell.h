@@ -14,8 +14,9 @@
  * K = K_b + K_m constant and assembled once on the device at shell_create, M the lumped mass. The membrane
  * is the corotated linear constant-strain triangle (the paper adopts a constant-strain triangle membrane,
  * Section 3); its constant matrix block is 2 (mu + lam) A t grad(phi_a).grad(phi_b) per triangle, with
- * mu = E / (2 (1 + nu)) and lam = E nu / (1 - nu^2). The linear system is solved by Jacobi-preconditioned
- * conjugate gradients on the GPU, either in FP64 or in FP32 with FP64 iterative refinement of the residual.
+ * mu = E / (2 (1 + nu)) and lam = E nu / (1 - nu^2). The linear system is solved by preconditioned conjugate
+ * gradients on the GPU (Jacobi, or a smoothed-aggregation multigrid cycle; the paper does not name its linear
+ * solver), either in FP64 or in FP32 with FP64 iterative refinement of the residual.
  *
  * Every step of the path runs in CUDA kernels: rest-state precompute (FP64), matrix assembly (FP64),
  * per-stencil forces, right-hand side, PCG, state update. There is no CPU fallback: without a usable
@@ -136,13 +137,15 @@ typedef struct shell_options {
                             * identical either way (same values, same order of operations); for measurement. */
 } shell_options;
 
-/* Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
+/* Solver options of the step (Section 5; the paper names no linear solver or tolerance, so these are this
+ * library's). Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
  * FP64 PCG, 1e-6 for the inner FP32 PCG, 1e-8 for the refinement: the FP32 force rounding, not the
  * solve, then bounds the error), pcg_max_it 20000, refine_max 20,
  * preconditioner AUTO. */
 void shell_default_options(shell_options *opt);
 
-/* Statistics of the last shell_step / shell_batch_step call for one instance. */
+/* Statistics of the last shell_step / shell_batch_step call for one instance (solver counters of the step of
+ * Section 5; no counterpart in the paper). */
 typedef struct shell_step_stats {
   int32_t steps_done;          /* steps committed by this call */
   int32_t pcg_iterations;      /* PCG iterations of the last committed step (summed over rounds) */
@@ -167,9 +170,11 @@ typedef struct shell_handle shell_handle;
 int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t model, const shell_bc *bc,
                  const shell_options *opt, shell_handle **out);
 
-/* Advance n_steps >= 0 steps. Each step: per-stencil forces at the current x, right-hand side, PCG (and
- * refinement), x += dt v'. A step that fails (NOT_CONVERGED, NONFINITE, TIMEOUT) is not committed and
- * ends the call; the steps before it are committed. stats may be NULL. */
+/* Advance n_steps >= 0 linearised backward-Euler steps (Section 5, Eq. 62-63). Each step: per-stencil forces at
+ * the current x, right-hand side, PCG (and refinement), v = v', x += dt v'. A step that fails (NOT_CONVERGED,
+ * NONFINITE, TIMEOUT) is not committed and ends the call; the steps before it are committed. stats may be NULL
+ * (else caller-owned). Synchronises the handle's stream. Errors: INVALID_ARG, BUSY (handle in a batch),
+ * NOT_CONVERGED, NONFINITE, TIMEOUT, OOM, CUDA. */
 int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
 
 /* The same steps as shell_step, for callers that cannot allocate device memory once their handles exist:
@@ -179,7 +184,8 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
  * allocates: its launch scratch (team schedule, barrier words, abort flag, status read-back) is a
  * file-scope static __device__ array of about 17 KB that every GPU loading the library holds until exit.
  * The paper has no counterpart to this; it is a deployment variant of shell_step.
- *   - Same arguments and results as shell_step (bit-identical states).
+ *   - Same arguments and results as shell_step (bit-identical states). It returns after its steps have
+ *     finished on the GPU (it synchronises the handle's stream to read the status back).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
  *     device current; make that first call before any stream capture.
  *   - The array is shared by every call in the process and keeps the last call's contents; the call clears
@@ -189,8 +195,6 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
  *     beyond that it returns SHELL_ERR_STATIC_LIMIT. */
 int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats);
 
-/* Energies at the current state, FP64: out[0] membrane, out[1] bending, out[2] kinetic 1/2 v^T M v,
- * out[3] external potential -sum f_ext . (x - X). */
 /* Exact backward Euler (Section 5, Eq. 62-63 without the linearisation): the new velocity v' solves
  * M (v' - v) = dt (f(x + dt v') + f_ext) at free vertices (v' = 0 at pinned ones), i.e. it minimises the
  * incremental potential. Each step runs a chord iteration with the constant matrix A = M + dt^2 K: v_0 = 0,
@@ -201,16 +205,36 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
  * alone or in its batch (a batch issues as many force + solve launches per step as its largest max_iters;
  * finished instances skip the later ones). Errors: INVALID_ARG (max_iters < 0, rtol < 0 or NaN), CUDA. */
 int shell_set_nonlinear(shell_handle *h, int32_t max_iters, double rtol);
+
+/* Energies at the current state x, v in FP64, summed over stencils in a fixed order:
+ *   out[0] membrane: corotated linear constant-strain triangles (Section 3), A t (mu |S - I|^2 + lam/2 tr(S - I)^2);
+ *   out[1] bending: Eq. 16 (edge hinge, shell: Eq. 23), Eq. 39 (FVM hinge, shell: Eq. 42), Eq. 52 (smoothed
+ *          hinge, shell: Eq. 54), per stencil 1/2 eps^T W eps, with the plate form of Eq. 20 / 41 / 53;
+ *   out[2] kinetic 1/2 v^T M v (lumped mass); out[3] external potential -sum f_ext . (x - X)
+ *          (the terms of the incremental potential of Section 5, Eq. 62).
+ * out: caller-allocated host array of 4 doubles. Synchronises the handle's stream (also allowed while the
+ * handle is in a batch, between batch steps). Errors: INVALID_ARG (NULL), CUDA. */
 int shell_energy(shell_handle *h, double out[4]);
 
-/* Elastic forces -grad(Psi_m + Psi_b) at the current x in FP64, written to out_xyz [V][3] (host). */
+/* Elastic forces f = -grad(Psi_m + Psi_b) at the current x in FP64, the force of the step's right-hand side:
+ * bending per stencil by Eq. 22 (edge hinge plate), Eq. 25-26 (edge hinge shell, normal derivative of App. B),
+ * Eq. 44-45 (FVM hinge), Eq. 56-57 (smoothed hinge), clamped-edge stencils per Eq. 30-31 and Eq. 59; membrane
+ * from the corotated constant-strain triangle (Section 3). Each vertex sums its stencils' contributions in a
+ * fixed order. out_xyz: caller-allocated host buffer [V][3], row-major. Synchronises the handle's stream.
+ * Errors: INVALID_ARG (NULL), CUDA. */
 int shell_forces(shell_handle *h, double *out_xyz);
 
-/* Apply the constant step matrix A = M + dt^2 (K_b + K_m) (identity rows / columns at pinned vertices; the
- * matrix is the scalar matrix (x) I_3) to in_xyz [V][3] in FP64: out_xyz = A in_xyz (host buffers). */
+/* Apply the constant step matrix A = M + dt^2 (K_b + K_m) of the linearised step (Section 5, Eq. 62-63; K_b
+ * the constant bending Hessian of Eq. 21 / 41 / 53, K_m the constant membrane block; identity rows / columns
+ * at pinned vertices; the matrix is the scalar matrix (x) I_3) to in_xyz [V][3] in FP64: out_xyz = A in_xyz.
+ * Both are caller-owned host buffers [V][3], row-major. Synchronises the handle's stream.
+ * Errors: INVALID_ARG (NULL), CUDA. */
 int shell_apply_matrix(shell_handle *h, const double *in_xyz, double *out_xyz);
 
-/* Copy the state to / from host buffers [V][3] (either pointer may be NULL to skip it). Each step's solver
+/* The state of the time integration (Section 5, Eq. 62-63): positions x and velocities v, held in FP64 on the
+ * device. Copy it to / from caller-owned host buffers [V][3], row-major (either pointer may be NULL to skip
+ * it). Both synchronise the handle's stream before they return. Setting a state clears a previous step failure
+ * of the handle. Errors: INVALID_ARG (h NULL), CUDA. Each step's solver
  * starts from the velocity extrapolated cubically from the last four committed steps
  * (4 (v + v_prev2) - 6 v_prev - v_prev3); setting a state keeps the three earlier velocities, since they
  * only shape the initial guess (results agree to the solve tolerance either way, and writing back an
@@ -218,7 +242,8 @@ int shell_apply_matrix(shell_handle *h, const double *in_xyz, double *out_xyz);
 int shell_get_state(shell_handle *h, double *x, double *v);
 int shell_set_state(shell_handle *h, const double *x, const double *v);
 
-/* Device-pointer variants: [V][3] row-major FP64 device buffers, stream ordered, no synchronisation. */
+/* Device-pointer variants of the state copies (Section 5's x and v): [V][3] row-major FP64 device buffers owned
+ * by the caller, stream ordered on the handle's stream, no synchronisation. Errors: INVALID_ARG (h NULL), CUDA. */
 int shell_get_state_device(shell_handle *h, double *d_x, double *d_v);
 int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v);
 
@@ -230,10 +255,15 @@ int shell_set_state_device(shell_handle *h, const double *d_x, const double *d_v
  * 0 without multigrid). */
 int shell_info(shell_handle *h, int64_t out[9]);
 
+/* Free the handle and all device memory it owns (after the handle's stream has finished its work). A handle in
+ * a batch must be retired first. Errors: INVALID_ARG (NULL), BUSY (still in a batch). */
 int shell_destroy(shell_handle *h);
+/* Static message of a SHELL_* code (never NULL; unknown codes give a generic message). */
 const char *shell_strerror(int code);
 
-/* Host-only mesh check (needs no GPU): builds the stencils and the matrix structure shell_create would
+/* Host-only mesh check (needs no GPU): builds the stencils of Section 4 (edge stencils of Section 4.3, Eq. 9-10
+ * and Eq. 31; triangle-centred stencils with virtual nodes of Section 4.4-4.5 and App. C, Eq. 78) and the matrix
+ * structure shell_create would
  * build and checks every index they hold. out[0] interior edge stencils (edge hinge models), out[1]
  * clamped edge stencils, out[2] triangle stencils with a virtual neighbour, out[3] structural nonzeros of
  * the scalar matrix, out[4] stored (SELL-padded) nonzeros, out[5] force contribution slots, out[6] local
@@ -243,7 +273,8 @@ int shell_topology_summary(int32_t n_verts, int32_t n_tris, const int32_t *tris,
                            const int32_t *clamped_edges, int32_t model, int64_t out[8]);
 
 /* ------------------------------------------------------------------------------------------ batch */
-/* A batch steps many independent handles together: one force launch and one persistent solve launch per
+/* The batch API has no counterpart in the paper: it runs the step of shell_step (Section 5, Eq. 62-63) for many
+ * independent simulations at once. A batch steps many independent handles together: one force launch and one persistent solve launch per
  * step for all resident instances, replayed from a CUDA graph. Instances are admitted while the batch's
  * device-memory budget (bytes of the admitted handles) allows; each instance's result does not depend on
  * the other instances in the batch. A handle admitted to a batch cannot be stepped alone until retired. */

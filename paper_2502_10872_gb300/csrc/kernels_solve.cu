@@ -30,6 +30,7 @@
 // d = 0 to a relative tolerance (or to a margin below the refinement target, if that is reached first);
 // v += d; repeat until ||r64|| <= refine_rtol ||b||.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "internal.h"
@@ -653,6 +654,9 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
 // multigrid preconditioner u is read from g and the new u = B r is computed by the V-cycle afterwards.
 // The solution x is accumulated in FP64 in both precisions (alpha_x: alpha in FP64): the recurrences never
 // read it, and in FP32 its rounding alone would leave the refinement's true residual above 1e-8 of ||b||.
+// In FP32 the recurrence r -= alpha s takes alpha rounded to FP32 while x takes the FP64 alpha, so x and the
+// recursive residual drift apart by about 2^-24 of each step; the FP64 residual of the next refinement round
+// is formed from x itself, so the drift is measured there and corrected like any other inner error.
 template <typename R>
 __device__ void phase_update(const Inst &I, const Team &tm, R alpha, R beta, bool first, double *x,
                              double alpha_x) {
@@ -1651,7 +1655,10 @@ static __device__ __align__(256) unsigned int g_static_scratch[kStaticWords];
 
 namespace {
 constexpr int kMaxDevices = 64;
-unsigned int *g_static_addr[kMaxDevices];   // device address of g_static_scratch, per device
+// device address of g_static_scratch, per device. Threads calling on different handles may fill an entry at
+// the same time: each then looks the address up itself (the same value) and stores it, so the entries are
+// atomics and the race is benign.
+std::atomic<unsigned int *> g_static_addr[kMaxDevices];
 }  // namespace
 
 cudaError_t static_scratch_setup(unsigned int **out) {
@@ -1659,13 +1666,15 @@ cudaError_t static_scratch_setup(unsigned int **out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_static_addr[dev]) {
+  unsigned int *a = g_static_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    g_static_addr[dev] = reinterpret_cast<unsigned int *>(p);
+    a = reinterpret_cast<unsigned int *>(p);
+    g_static_addr[dev].store(a, std::memory_order_release);
   }
-  *out = g_static_addr[dev];
+  *out = a;
   return cudaSuccess;
 }
 
