@@ -17,6 +17,8 @@ Layout:
   material matrices.
 * :mod:`oracle.energies`  -- per-stencil bending energies and exact gradients for the six models
   (Eq. 16-26, Eq. 39-45, Eq. 52-57, App. B) and the corotated constant-strain membrane.
+* :mod:`oracle.appendix_d` -- App. D's world-frame edge-hinge models QTP and QTS and the Quadratic/Cubic
+  shell energy (Eq. 79-89), written from App. D's printed operator.
 * :mod:`oracle.system`    -- lumped mass, the constant matrix M + dt^2 (K_b + K_m), the linearised
   backward-Euler step (Section 5, Eq. 62-63), the exact backward-Euler step by chord iteration with its
   residual and incremental potential, and energy totals.
