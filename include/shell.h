@@ -319,6 +319,13 @@ int shell_batch_autotune(shell_batch *b, int32_t steps_per_trial, double *out_ms
  * re-planned at the next step; results do not depend on the shape. Errors: INVALID_ARG. */
 int shell_batch_set_launch(shell_batch *b, int32_t ctas_per_sm, int32_t share_x100, int32_t clusters);
 int shell_batch_kernel_times(shell_batch *b, double out_ms[2]);
+/* Bound of every device-side wait at a team barrier of this batch's solve launches, in nanoseconds (ns <= 0
+ * restores the default, 4 s). A CTA whose wait exceeds it raises the launch's abort flag and leaves; the other
+ * CTAs leave at their next barrier or before they write any state, so the abandoned launch commits nothing
+ * and shell_batch_step returns SHELL_ERR_TIMEOUT, with stats[k].steps_done the steps committed before it; the
+ * batch resets its barrier words, and the next call steps normally. For callers that must bound the latency
+ * of a stalled step (no counterpart in the paper). Errors: INVALID_ARG (NULL). */
+int shell_batch_set_wait_limit(shell_batch *b, int64_t ns);
 int shell_batch_destroy(shell_batch *b);
 
 #ifdef __cplusplus

@@ -41,7 +41,7 @@ EXPORTS = (
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
     "shell_batch_autotune", "shell_batch_set_launch", "shell_batch_get_states", "shell_batch_set_states",
-    "shell_batch_state_layout",
+    "shell_batch_state_layout", "shell_batch_set_wait_limit",
     "shell_batch_destroy",
 )
 
@@ -138,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_get_states": (C.c_int, [P, P, P]),
         "shell_batch_set_states": (C.c_int, [P, P, P]),
         "shell_batch_state_layout": (C.c_int, [P, P, P]),
+        "shell_batch_set_wait_limit": (C.c_int, [P, C.c_int64]),
         "shell_batch_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
@@ -461,6 +462,11 @@ def shell_batch_kernel_times(b: Batch) -> np.ndarray:
     out = np.zeros(2, np.float64)
     _check(load_library().shell_batch_kernel_times(b.ptr, out.ctypes.data), "shell_batch_kernel_times")
     return out
+
+
+def shell_batch_set_wait_limit(b: Batch, ns: int = 0):
+    """Bound of a team-barrier wait of the batch's solve launches in ns (<= 0: the default, 4 s)."""
+    _check(load_library().shell_batch_set_wait_limit(b.ptr, int(ns)), "shell_batch_set_wait_limit")
 
 
 def shell_batch_autotune(b: Batch, steps_per_trial: int = 2) -> dict:

@@ -180,6 +180,7 @@ struct shell_batch {
   double share_scale = 1.0;    // multiplier of the CTA share given to large instances
   std::vector<cudaEvent_t> pev;   // 3 per profiled step
   double kern_ms[2] = {0.0, 0.0};
+  unsigned long long wait_ns = (unsigned long long)kMaxTeamWaitMs * 1000000ull;   // team-barrier wait bound
 };
 
 namespace {
@@ -479,6 +480,7 @@ int rebuild_tables(shell_batch *b) {
 // team layout stays valid: whole-cluster teams become flat global-barrier teams)
 cudaError_t solve_launch(shell_batch *b, cudaStream_t st, int chord_k) {
   b->sched.chord_k = chord_k;
+  b->sched.wait_ns = b->wait_ns;
   cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, b->occ_launch, st);
   if (e != cudaSuccess && b->sched.cluster > 0) {
     cudaGetLastError();
@@ -1661,6 +1663,13 @@ int shell_batch_set_launch(shell_batch *b, int32_t ctas_per_sm, int32_t share_x1
 int shell_batch_set_profiling(shell_batch *b, int32_t on) {
   if (!b) return SHELL_ERR_INVALID_ARG;
   b->profiling = on != 0;
+  return SHELL_OK;
+}
+
+int shell_batch_set_wait_limit(shell_batch *b, int64_t ns) {
+  if (!b) return SHELL_ERR_INVALID_ARG;
+  b->wait_ns = ns > 0 ? (unsigned long long)ns : (unsigned long long)kMaxTeamWaitMs * 1000000ull;
+  destroy_graph(b);   // the captured launches hold the previous bound
   return SHELL_OK;
 }
 

@@ -19,7 +19,7 @@ namespace shl {
 constexpr int kSlice = 32;          // SELL slice height (one warp)
 constexpr int kBlock = 256;         // threads of every CTA of the persistent solve kernel
 constexpr int kForceBlock = 128;    // threads of a force tile
-constexpr int kMaxTeamWaitMs = 4000;  // bounded spin of the team barrier
+constexpr int kMaxTeamWaitMs = 4000;  // default bound of a team-barrier wait (Sched::wait_ns)
 constexpr int kBarWords = 64;       // barrier words per team: arrival count at [0], generation at [32]
                                     // (separate 128-byte lines, so spinning readers do not contend with
                                     // the arrival atomics)
@@ -194,6 +194,7 @@ struct Sched {
   int32_t cluster;       // CTAs per cluster of the launch, 0 = no clusters
   int32_t halo_cap;      // vector entries the launch's dynamic shared memory stages (set by launch_solve)
   int32_t chord_k;       // chord iteration of the step this launch performs (0: the first, or the only one)
+  unsigned long long wait_ns;  // bound of a team-barrier wait (ns); past it the CTA raises the abort flag
 };
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)

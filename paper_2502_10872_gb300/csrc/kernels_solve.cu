@@ -65,6 +65,7 @@ struct Team {
   unsigned long long t0;   // start of the current instance's solve (global timer, ns)
   int cap;      // vector entries the dynamic shared memory can stage (0: no staging)
   int chord_k;  // chord iteration of the step this launch performs
+  unsigned long long wait_ns;   // bound of a barrier wait
 };
 
 __device__ inline void cluster_barrier() {
@@ -94,7 +95,7 @@ __device__ int global_arrive_wait(const Team &tm, unsigned int parties) {
     atomicAdd(gen, 1u);
   } else {
     const unsigned long long t0 = gtimer();
-    const unsigned long long limit = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
+    const unsigned long long limit = tm.wait_ns;
     while (ld_acquire(gen) == g) {
       if (ld_volatile_i(tm.abort_flag)) return 0;
       if (gtimer() - t0 > limit) {
@@ -1353,13 +1354,18 @@ __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, in
 // End of one solve of a step. Linearised step (nl_max <= 1): commit v, x. Exact backward Euler: commit
 // when the chord iteration met its tolerance before this solve (done_early) or used its nl_max solves,
 // else hand off to the next iteration. bb: ||b||^2 of this solve (at k = 0: ||R(0)||^2).
-__device__ void finish_step(const Inst &I, const Team &tm, double bb, int iters, int rounds, double rel,
+// Returns false, writing nothing, if a bounded wait of the launch has given up: a CTA that timed out leaves
+// the launch, and its team mates may still pass the barrier before the commit (its last arrival completes
+// it), so every CTA checks the abort flag once before it writes the state; an abandoned launch then commits
+// nothing.
+__device__ bool finish_step(const Inst &I, const Team &tm, double bb, int iters, int rounds, double rel,
                             bool done_early) {
   const int k = tm.chord_k;
+  if (ld_volatile_i(tm.abort_flag)) return false;
   if (I.nl_max <= 1) {
     phase_commit(I, tm);
     set_status(I, tm, SHELL_OK, iters, rounds, rel);
-    return;
+    return true;
   }
   const int solves = done_early ? k : k + 1;
   const bool last = done_early || solves >= I.nl_max;
@@ -1388,6 +1394,7 @@ __device__ void finish_step(const Inst &I, const Team &tm, double bb, int iters,
       s->nl_flags = 1;
     }
   }
+  return true;
 }
 
 // returns false if the kernel must stop (abort). Chord iteration k > 0 of an exact backward-Euler step: the
@@ -1437,8 +1444,7 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
     for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
     ROWS_END
   }
-  finish_step(I, tm, bb, iters, 0, ref > 0.0 ? sqrt(rho / ref) : 0.0, early);
-  return true;
+  return finish_step(I, tm, bb, iters, 0, ref > 0.0 ? sqrt(rho / ref) : 0.0, early);
 }
 
 __device__ bool solve_fp32r(const Inst &I, Team &tm) {
@@ -1504,8 +1510,7 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
     for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
     ROWS_END
   }
-  finish_step(I, tm, bb, total, rounds, rel, early);
-  return true;
+  return finish_step(I, tm, bb, total, rounds, rel, early);
 }
 
 // PREC: 0 = instances of either precision, 1 = FP64 instances only, 2 = FP32-refinement instances only.
@@ -1525,6 +1530,7 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
   tm.cluster_ok = sch.cluster_ok;
   tm.cap = sch.halo_cap;
   tm.chord_k = sch.chord_k;
+  tm.wait_ns = sch.wait_ns;
   if (tm.size == 1)
     tm.mode = 0;
   else if (sch.cluster > 0 && tm.size % sch.cluster == 0)
@@ -1702,6 +1708,7 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   sc.n_ctas = team_ctas;
   sc.cluster = 0;
   sc.cluster_ok = nullptr;
+  sc.wait_ns = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
   static thread_local int32_t host_tab[2 * kStaticMaxCtas + 4];
   for (int c = 0; c < team_ctas; ++c) {
     host_tab[c] = 0;
