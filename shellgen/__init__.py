@@ -339,3 +339,28 @@ def simply_supported_square(n: int, size: float = 8.0, mesh: str = "regular"):
     else:
         raise ValueError(mesh)
     return flat3(xy), tris, bmask
+
+
+def cantilever(model: str = "FP", nx: int = 16, ny: int = 2, length: float = 10.0, width: float = 1.0,
+               E: float = 1.2e6, nu: float = 0.1, thickness: float = 0.1, total_load: float = 4.0,
+               density: float = 1.0, dt: float = 1.0) -> Scenario:
+    """Cantilever under end shear (Section 6.1, geometrically non-linear benchmark): a flat ``length`` x
+    ``width`` plate meshed with (nx + 1) x (ny + 1) nodes (17 x 3 = 51 by default; cells split along
+    (i, j) -> (i + 1, j + 1)), the two node columns at x = 0 pinned, ``total_load`` shared equally by the
+    right-edge nodes along +z, no gravity, no clamped edges (all boundary edges are free for bending).
+    ``density`` and ``dt`` only enter a quasi-static solve through the mass shift M / dt^2 of its linear
+    systems (negligible by default: about 1e-7 of the stiffness)."""
+    xy, tris = grid(nx, ny, length, width)
+    rest = flat3(xy)
+    V = rest.shape[0]
+    pinned = (xy[:, 0] < length / nx * (1.0 + 1e-9)).astype(np.uint8)
+    right = np.flatnonzero(np.abs(xy[:, 0] - length) < 1e-9 * length).astype(np.int32)
+    lf = np.tile([0.0, 0.0, total_load / len(right)], (len(right), 1))
+    return Scenario(f"cantilever_{model}", tris, rest, rest.copy(), np.zeros_like(rest), model, E, nu, thickness,
+                    density, pinned, np.zeros((0, 2), np.int32), (0.0, 0.0, 0.0), right, lf, dt, 1)
+
+
+def cantilever_tip(sc: Scenario) -> int:
+    """Index of the mid node of the cantilever's loaded edge (where w_tip is read)."""
+    right = np.asarray(sc.load_vtx)
+    return int(right[np.argsort(sc.rest[right, 1])[len(right) // 2]])
