@@ -4,7 +4,8 @@ Workload (default ``batch256``): 256 independent instances, grid side log-unifor
 plates (1 m square, one edge clamped) and half 90-degree cylinder panels (radius U(0.3, 2), both straight
 edges clamped), bending model uniform over the six, E log-uniform in [1e5, 1e8] Pa, nu U(0.2, 0.45),
 thickness 1e-3 m, density 1000 kg/m^3, gravity, dt = 1e-2 s. All instances are stepped together: per step
-one force launch and one persistent solve launch (graph-replayed when not profiling).
+one persistent launch (forces, right-hand side, solve and commit of every instance; graph-replayed when not
+profiling).
 
 Printed line (one JSON object, rank 0):
   value      vertex-steps/s of the batched FP32 + FP64-refinement path (device-timed, inputs resident),
@@ -14,7 +15,8 @@ Printed line (one JSON object, rank 0):
   latency    p50 / p99 per-step device time of the batch,
   e2e        the same metric through the public C ABI with host buffers (per step: host->device state of
              every instance from pinned memory, the step, device->host state),
-  roofline   the solve kernel (dominant): algorithmic bytes per launch / mean launch time vs measured HBM,
+  roofline   the step kernel (the only launch of a step): algorithmic bytes per launch / mean launch time vs
+             measured HBM,
   cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload.
 
 ``--impl reference`` times the FP64 CPU oracle alone on the same workload (bounded sample per step).
@@ -197,10 +199,25 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------------------------ bytes model
-def algorithmic_bytes(info, stats, steps):
-    """Compulsory DRAM bytes of the solve kernel (FP32 + refinement) for ``steps`` steps of one instance.
+def force_bytes(info):
+    """Compulsory DRAM bytes of one FP32 force phase of an instance (every solve of a step evaluates the
+    forces once): per triangle stencil of the FVM and smoothed hinges 244 B (6 indices, 18 L, 6 W, 3 kappa0,
+    3 Dm^-1, 3 FP64 rest Gram entries, the area, and 6 contribution slots of 12 B written), per membrane-only
+    triangle of the edge-hinge models 88 B, per edge stencil 89 B, plus 24 B per vertex (the FP64 positions,
+    read once). 0 if the model is not given."""
+    model = info.get("model")
+    if model is None:
+        return 0.0
+    V, T, S = info["n_verts"], info["n_tris"], info["n_stencils"]
+    if model in ("EP", "ES"):
+        return 88.0 * T + 89.0 * S + 24.0 * V
+    return 244.0 * T + 24.0 * V
 
-    Per step: right-hand side 16 B per contribution slot (FP32 force + its index) + 213 B per row (reads:
+
+def algorithmic_bytes(info, stats, steps):
+    """Compulsory DRAM bytes of the step kernel (FP32 + refinement) for ``steps`` steps of one instance.
+
+    Per step: the force phase (``force_bytes``), right-hand side 16 B per contribution slot (FP32 force + its index) + 213 B per row (reads:
     incidence pointer 4, pinned 1, mass 8, v, f_ext and the three earlier velocities of the warm start 5 x 24;
     writes: b, the initial guess and its AoS copy 24 + 24 + 32), commit 240 B per row (reads the solution,
     v, v_prev, v_prev2, x; writes v_prev3, v_prev2, v_prev, v, x; 24 B each). Per refinement round: FP64
@@ -217,7 +234,7 @@ def algorithmic_bytes(info, stats, steps):
     V, nnz, slots = info["n_verts"], info["nnz"], info["n_slots"]
     vc = float(info.get("vcycle_bytes", 0))
     solves = max(1, int(stats.get("nl_iterations", 0)))
-    per_step = (solves * 16.0 * slots + (213.0 + 240.0) * V
+    per_step = (solves * (16.0 * slots + force_bytes(info)) + (213.0 + 240.0) * V
                 + (solves - 1) * (12.0 * nnz + (32.0 + 109.0 + 104.0) * V))
     per_round = 12.0 * nnz + 240.0 * V + vc
     per_iter = 8.0 * nnz + 192.0 * V + vc
@@ -390,7 +407,7 @@ def main():
     p50, p99 = float(np.percentile(times32, 50)), float(np.percentile(times32, 99))
 
     # ---- roofline of the solve kernel
-    infos = [gb.shell_info(h) for h in h32]
+    infos = [dict(gb.shell_info(h), model=sc.model) for h, sc in zip(h32, scs)]
     algo = sum(algorithmic_bytes(infos[k], stats32[k], K) for k in range(len(h32)))
     solve_s = kern32[1] / 1000.0
     achieved = algo / K / (solve_s / K) / 1e9
@@ -398,10 +415,10 @@ def main():
     # DRAM traffic of one steady-state launch from a committed ncu capture, with that launch's own
     # algorithmic bytes (its iteration counts differ a little from the timed steps' mean)
     traffic, traffic_algo = measured_traffic(args.workload)
-    # per step: one FP32 force launch over all instances and one persistent solve launch (per chord iteration)
+    # per step: one persistent launch (forces, right-hand side, solve, commit), per chord iteration
     lps = int(args.nonlinear.split(",")[0]) if args.nonlinear else 1
     lps = max(1, lps)
-    n_launch = K * 2 * lps
+    n_launch = K * lps
 
     # ---- plain FP64 on the same batch, same steps
     fp64 = None
@@ -483,7 +500,7 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "traffic_launch_algorithmic_bytes": traffic_algo,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo / (K * lps), "mean_launch_ms": kern32[1] / (K * lps),
-                     "force_kernel_ms_per_step": kern32[0] / K},
+                     "phases": "forces, right-hand side, PCG with refinement, commit: one launch per step"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),
         "wall_s_timed": wall32,
     }

@@ -206,6 +206,30 @@ int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats
  * finished instances skip the later ones). Errors: INVALID_ARG (max_iters < 0, rtol < 0 or NaN), CUDA. */
 int shell_set_nonlinear(shell_handle *h, int32_t max_iters, double rtol);
 
+/* Newton's method for the iterations of shell_set_nonlinear (Section 5: the incremental potential is minimised
+ * by a Newton-type solver): with on != 0 each iteration solves with the tangent J(v_k) = M + dt^2 (K_b +
+ * sum_t H_t(x_t + dt v_k)) instead of the constant matrix, K_b the constant bending Hessian (Eq. 21, 41, 53;
+ * also for the shell models, so their iteration converges at a linear rate) and H_t the Hessian of triangle
+ * t's corotated membrane energy at the iterate, in closed form with its two rotation terms clamped at zero
+ * (positive semi-definite). The preconditioner stays that of the constant matrix. A batch holding a Newton
+ * instance runs a solve variant that carries the tangent. Takes effect at the next step. Errors: INVALID_ARG,
+ * CUDA. */
+int shell_set_newton(shell_handle *h, int32_t on);
+
+/* Quasi-static equilibrium (Section 5, Eq. 64): from the current positions, find x with f(x) + f_ext = 0 at the
+ * free vertices (pinned ones stay) by Newton-Raphson in one load step: x_{k+1} = x_k + alpha dx with
+ * (K_T(x_k) + M / dt^2) dx = f(x_k) + f_ext, K_T the tangent of shell_set_newton, alpha = min(1, eps_u /
+ * max_i |dx_i|) (the incremental displacement limit; eps_u = 0: no limit), until ||f(x_k) + f_ext|| < eps_f
+ * (2-norm over the free degrees of freedom). The mass shift M / dt^2 (the handle's dt and density) damps the
+ * steps and leaves the equilibrium unchanged; a small density or a large dt makes it negligible. At most
+ * max_iters Newton steps. On success x is the equilibrium and v = 0; stats (may be NULL): nl_iterations =
+ * Newton steps, rel_residual = ||f + f_ext|| reached, pcg_iterations summed over the steps. If the residual
+ * is still above eps_f after max_iters steps, nothing is committed and SHELL_ERR_NOT_CONVERGED is returned
+ * (cleared by shell_set_state). The handle's settings of shell_set_nonlinear / shell_set_newton are kept.
+ * Synchronises the handle's stream. Errors: INVALID_ARG (eps_f <= 0, eps_u < 0, max_iters < 1), BUSY (handle
+ * in a batch), NOT_CONVERGED, NONFINITE, TIMEOUT, CUDA. */
+int shell_solve_static(shell_handle *h, double eps_f, double eps_u, int32_t max_iters, shell_step_stats *stats);
+
 /* Energies at the current state x, v in FP64, summed over stencils in a fixed order:
  *   out[0] membrane: corotated linear constant-strain triangles (Section 3), A t (mu |S - I|^2 + lam/2 tr(S - I)^2);
  *   out[1] bending: Eq. 16 (edge hinge, shell: Eq. 23), Eq. 39 (FVM hinge, shell: Eq. 42), Eq. 52 (smoothed
@@ -274,8 +298,10 @@ int shell_topology_summary(int32_t n_verts, int32_t n_tris, const int32_t *tris,
 
 /* ------------------------------------------------------------------------------------------ batch */
 /* The batch API has no counterpart in the paper: it runs the step of shell_step (Section 5, Eq. 62-63) for many
- * independent simulations at once. A batch steps many independent handles together: one force launch and one persistent solve launch per
- * step for all resident instances, replayed from a CUDA graph. Instances are admitted while the batch's
+ * independent simulations at once. A batch steps many independent handles together: one persistent launch per
+ * step for all resident instances (per-stencil forces, right-hand side, solve and commit; FP64 instances take
+ * their forces from one force launch just before it), replayed from a CUDA graph. Instances are admitted while
+ * the batch's
  * device-memory budget (bytes of the admitted handles) allows; each instance's result does not depend on
  * the other instances in the batch. A handle admitted to a batch cannot be stepped alone until retired. */
 typedef struct shell_batch shell_batch;
@@ -299,10 +325,10 @@ int shell_batch_state_layout(shell_batch *b, int32_t *slots, int64_t *row_offset
 /* Device time of the last shell_batch_step, per step, in milliseconds: out[k] for k < n (n <= steps). */
 int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
 /* Kernel timing of later shell_batch_step calls: with on != 0 every step is launched directly (not from
- * the graph) with CUDA events around the force launches and the solve launch (of every chord iteration of
- * an exact backward-Euler step). shell_batch_kernel_times
- * then gives out_ms[0] = summed force-kernel time and out_ms[1] = summed solve-kernel time of the last
- * call, in milliseconds. */
+ * the graph) with CUDA events around the force launch of FP64 instances and the step launch (of every chord
+ * iteration of an exact backward-Euler step). shell_batch_kernel_times then gives out_ms[0] = summed time of
+ * the FP64 force launches (0 for a batch of FP32-refinement instances, whose forces are a phase of the step
+ * launch) and out_ms[1] = summed time of the step launches of the last call, in milliseconds. */
 int shell_batch_set_profiling(shell_batch *b, int32_t on);
 /* Autotune the persistent solve launch of this batch: flat teams (any size, global barriers, cooperative
  * launch) with 3 occupancies (CTAs per SM: 1, half, the maximum) x 3 CTA shares for large instances (x0.5,

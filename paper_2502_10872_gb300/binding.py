@@ -41,7 +41,7 @@ EXPORTS = (
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
     "shell_batch_autotune", "shell_batch_set_launch", "shell_batch_get_states", "shell_batch_set_states",
-    "shell_batch_state_layout", "shell_batch_set_wait_limit",
+    "shell_batch_state_layout", "shell_batch_set_wait_limit", "shell_set_newton", "shell_solve_static",
     "shell_batch_destroy",
 )
 
@@ -139,6 +139,8 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_set_states": (C.c_int, [P, P, P]),
         "shell_batch_state_layout": (C.c_int, [P, P, P]),
         "shell_batch_set_wait_limit": (C.c_int, [P, C.c_int64]),
+        "shell_set_newton": (C.c_int, [P, C.c_int32]),
+        "shell_solve_static": (C.c_int, [P, C.c_double, C.c_double, C.c_int32, P]),
         "shell_batch_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
@@ -308,6 +310,23 @@ def shell_step(h: Handle, n_steps: int = 1, check: bool = True) -> dict:
 def shell_set_nonlinear(h: Handle, max_iters: int, rtol: float = 1e-8):
     """Exact backward Euler by chord iteration: up to max_iters solves per step (<= 1: linearised step)."""
     _check(load_library().shell_set_nonlinear(h.ptr, int(max_iters), float(rtol)), "shell_set_nonlinear")
+
+
+def shell_set_newton(h: Handle, on: bool = True):
+    """Newton iterations (tangent of the corotated membrane) for the handle's exact backward-Euler steps."""
+    _check(load_library().shell_set_newton(h.ptr, 1 if on else 0), "shell_set_newton")
+
+
+def shell_solve_static(h: Handle, eps_f: float = 1e-3, eps_u: float = 0.1, max_iters: int = 1000,
+                       check: bool = True) -> dict:
+    """Quasi-static equilibrium (Eq. 64) by Newton-Raphson with the displacement limit eps_u."""
+    st = shell_step_stats()
+    rc = load_library().shell_solve_static(h.ptr, float(eps_f), float(eps_u), int(max_iters), C.byref(st))
+    if check:
+        _check(rc, "shell_solve_static")
+    d = st.as_dict()
+    d["rc"] = rc
+    return d
 
 
 def shell_step_noalloc(h: Handle, n_steps: int = 1, check: bool = True) -> dict:

@@ -152,8 +152,8 @@ struct shell_batch {
   void *tbl = nullptr;
   size_t tbl_bytes = 0;
   Inst *d_insts = nullptr;
-  Tile *d_tiles64 = nullptr, *d_tiles32 = nullptr;
-  int n_tiles64 = 0, n_tiles32 = 0;
+  Tile *d_tiles64 = nullptr;   // force tiles of FP64 instances
+  int n_tiles64 = 0;
   Sched sched{};
   int grid = 0;
   int prec = 0;     // solve-kernel variant: 0 mixed, 1 FP64 only, 2 FP32-refinement only
@@ -189,7 +189,8 @@ namespace {
 // compute the same value).
 // CTAs per SM of the solve variant compiled for `occ` (FP32: variants for 3, 4, 5; others one variant)
 int blocks_per_sm_cached(int prec, int occ = 3) {
-  static std::atomic<int> n[3][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}};
+  static std::atomic<int> n[4][6] = {{-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1},
+                                     {-1, -1, -1, -1, -1, -1}};
   occ = std::max(1, std::min(5, occ));
   int v = n[prec][occ].load();
   if (v < 0) {
@@ -200,7 +201,7 @@ int blocks_per_sm_cached(int prec, int occ = 3) {
 }
 int max_occ(int prec) { return prec == 2 ? blocks_per_sm_cached(2, 5) : blocks_per_sm_cached(prec, 2); }
 int max_clusters_cached(int prec) {
-  static std::atomic<int> n[3] = {-1, -1, -1};
+  static std::atomic<int> n[4] = {-1, -1, -1, -1};
   int v = n[prec].load();
   if (v < 0) {
     v = std::max(0, solve_max_clusters(prec, kCluster));
@@ -243,20 +244,26 @@ int rebuild_tables(shell_batch *b) {
     return SHELL_OK;
   }
   std::vector<Inst> insts(n);
-  std::vector<Tile> t64, t32;
+  std::vector<Tile> t64;   // force tiles of the FP64 instances (FP32 ones evaluate forces in the step kernel)
   for (int k = 0; k < n; ++k) {
     shell_handle *h = b->slots[b->active[k]];
     insts[k] = h->h;
+    if (h->h.precision != SHELL_FP64) continue;
     for (Tile t : h->tiles) {
       t.inst = k;
-      (h->h.precision == SHELL_FP64 ? t64 : t32).push_back(t);
+      t64.push_back(t);
     }
   }
   // ---- solve-kernel variant by the precisions present, then the schedule: teams of CTAs, each working
   // through a list of instances
-  bool any64 = false, any32 = false;
-  for (int k = 0; k < n; ++k) (b->slots[b->active[k]]->h.precision == SHELL_FP64 ? any64 : any32) = true;
-  b->prec = (any64 && any32) ? 0 : (any64 ? 1 : 2);
+  bool any64 = false, any32 = false, anynt = false;
+  for (int k = 0; k < n; ++k) {
+    const Inst &hk = b->slots[b->active[k]]->h;
+    (hk.precision == SHELL_FP64 ? any64 : any32) = true;
+    anynt = anynt || (hk.nl_newton && hk.nl_max > 1);
+  }
+  // a batch with a Newton instance runs the variant that carries the Newton tangent
+  b->prec = anynt ? 3 : (any64 && any32) ? 0 : (any64 ? 1 : 2);
   // default occupancy: the 3-CTA variant for FP32 (fewest spills), else the variant's maximum
   const int occ_def = b->prec == 2 ? blocks_per_sm_cached(2, 3) : max_occ(b->prec);
   const int occ = (b->occ > 0) ? std::min(b->occ, max_occ(b->prec)) : occ_def;
@@ -426,7 +433,6 @@ int rebuild_tables(shell_batch *b) {
   auto layout = [&](Carver &C) {
     b->d_insts = C.take<Inst>(n);
     b->d_tiles64 = C.take<Tile>(t64.size());
-    b->d_tiles32 = C.take<Tile>(t32.size());
     b->sched.cta_team = C.take<int32_t>(grid);
     b->sched.cta_rank = C.take<int32_t>(grid);
     b->sched.team_size = C.take<int32_t>(n_teams);
@@ -457,7 +463,6 @@ int rebuild_tables(shell_batch *b) {
   cudaStream_t st = b->mem.st;
   CK(cudaMemcpyAsync(b->d_insts, insts.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice, st));
   if (!t64.empty()) CK(cudaMemcpyAsync(b->d_tiles64, t64.data(), sizeof(Tile) * t64.size(), cudaMemcpyHostToDevice, st));
-  if (!t32.empty()) CK(cudaMemcpyAsync(b->d_tiles32, t32.data(), sizeof(Tile) * t32.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.cta_team, cta_team.data(), 4 * grid, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.cta_rank, cta_rank.data(), 4 * grid, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
@@ -471,7 +476,6 @@ int rebuild_tables(shell_batch *b) {
   CK(cudaMemsetAsync(b->sched.abort_flag, 0, sizeof(int32_t), st));
   CK(cudaStreamSynchronize(st));   // host vectors above go out of scope
   b->n_tiles64 = (int)t64.size();
-  b->n_tiles32 = (int)t32.size();
   b->dirty = false;
   return SHELL_OK;
 }
@@ -491,13 +495,13 @@ cudaError_t solve_launch(shell_batch *b, cudaStream_t st, int chord_k) {
   return e;
 }
 
-// one step: forces and solve, repeated for the chord iterations of exact backward-Euler instances
-// (instances whose step is done skip the later launches)
+// one step: one persistent launch (forces, right-hand side, solve, commit of every FP32-refinement instance;
+// FP64 instances take their forces from a force launch just before it), repeated for the chord iterations of
+// exact backward-Euler instances (instances whose step is done skip the later launches)
 int launch_step(shell_batch *b) {
   cudaStream_t st = b->mem.st;
   for (int k = 0; k < b->chord_max; ++k) {
     CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));
-    CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st, k));
     CK(solve_launch(b, st, k));
   }
   return SHELL_OK;
@@ -566,8 +570,7 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       for (int k = 0; k < b->chord_max; ++k) {
         const int e0 = pev_per_step * s + 3 * k;
         CK(cudaEventRecord(b->pev[e0], st));
-        CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));
-        CK(launch_forces(b->d_insts, b->d_tiles32, b->n_tiles32, 0, 1, st, k));
+        CK(launch_forces(b->d_insts, b->d_tiles64, b->n_tiles64, 0, 0, st, k));   // FP64 instances only
         CK(cudaEventRecord(b->pev[e0 + 1], st));
         CK(solve_launch(b, st, k));
         CK(cudaEventRecord(b->pev[e0 + 2], st));
@@ -1037,6 +1040,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.vprev2 = C.take<double>(3 * (size_t)nv);
     I.vprev3 = C.take<double>(3 * (size_t)nv);
     I.xk = C.take<double>(3 * (size_t)nv);
+    I.vk = C.take<double>(3 * (size_t)nv);
     I.rest = C.take<double>(3 * (size_t)nv);
     I.fext = C.take<double>(3 * (size_t)nv);
     I.mass = C.take<double>(nv);
@@ -1057,6 +1061,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.m_G64 = C.take<double>(3 * (size_t)nt);
     I.m_At64 = C.take<double>(nt);
     I.m_At32 = C.take<float>(nt);
+    I.m_T = C.take<double>(10 * (size_t)nt);
     I.e_idx = C.take<int32_t>(4 * (size_t)ne);
     I.e_mode = C.take<uint8_t>(ne);
     I.e_L64 = C.take<double>(4 * (size_t)ne);
@@ -1241,14 +1246,15 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
 int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
   if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
-  const int prec = h->h.precision == SHELL_FP64 ? 1 : 2;
+  const bool newton = h->h.nl_newton && h->h.nl_max > 1;
+  const int prec = newton ? 3 : (h->h.precision == SHELL_FP64 ? 1 : 2);
   int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(prec, prec == 2 ? 3 : 2), h->h.n_chunks));
   if (team > static_max_ctas()) return SHELL_ERR_STATIC_LIMIT;
   const InstStatus before = h->last_status;
   InstStatus after{};
   int32_t aborted = 0;
-  cudaError_t e = launch_step_static(h->d_inst, h->d_tiles, (int)h->tiles.size(), h->h.precision != SHELL_FP64, team,
-                                     n_steps, std::max(1, h->h.nl_max), &after, &aborted, h->mem.st);
+  cudaError_t e = launch_step_static(h->d_inst, h->d_tiles, (int)h->tiles.size(), h->h.precision != SHELL_FP64,
+                                     newton, team, n_steps, std::max(1, h->h.nl_max), &after, &aborted, h->mem.st);
   if (e != cudaSuccess) {
     last_cuda_error() = e;
     return SHELL_ERR_CUDA;
@@ -1291,6 +1297,44 @@ int shell_set_nonlinear(shell_handle *h, int32_t max_iters, double rtol) {
   if (h->batch) h->batch->dirty = true;
   if (h->solo) h->solo->dirty = true;
   return SHELL_OK;
+}
+
+int shell_set_newton(shell_handle *h, int32_t on) {
+  if (!h) return SHELL_ERR_INVALID_ARG;
+  h->h.nl_newton = on ? 1 : 0;
+  CK(cudaMemcpyAsync(h->d_inst, &h->h, sizeof(Inst), cudaMemcpyHostToDevice, h->mem.st));
+  CK(cudaStreamSynchronize(h->mem.st));
+  if (h->batch) h->batch->dirty = true;
+  if (h->solo) h->solo->dirty = true;
+  return SHELL_OK;
+}
+
+// Eq. 64 quasi-static Newton-Raphson: one step of the handle's iteration machinery in its static mode (no
+// inertia in the residual, Newton tangent, eps_u limiter, absolute residual test), then the handle's
+// nonlinear settings are restored
+int shell_solve_static(shell_handle *h, double eps_f, double eps_u, int32_t max_iters, shell_step_stats *stats) {
+  if (!h || !(eps_f > 0.0) || !(eps_u >= 0.0) || max_iters < 1) return SHELL_ERR_INVALID_ARG;
+  if (h->batch) return SHELL_ERR_BUSY;
+  const Inst saved = h->h;
+  h->h.nl_max = max_iters + 1;   // up to max_iters solves, then a launch that tests the last iterate
+  h->h.nl_rtol = 0.0;
+  h->h.nl_atol = eps_f;
+  h->h.nl_eps_u = eps_u;
+  h->h.nl_newton = 1;
+  h->h.nl_static = 1;
+  CK(cudaMemcpyAsync(h->d_inst, &h->h, sizeof(Inst), cudaMemcpyHostToDevice, h->mem.st));
+  if (h->solo) h->solo->dirty = true;
+  const int rc = shell_step(h, 1, stats);
+  h->h.nl_max = saved.nl_max;
+  h->h.nl_rtol = saved.nl_rtol;
+  h->h.nl_atol = saved.nl_atol;
+  h->h.nl_eps_u = saved.nl_eps_u;
+  h->h.nl_newton = saved.nl_newton;
+  h->h.nl_static = saved.nl_static;
+  CK(cudaMemcpyAsync(h->d_inst, &h->h, sizeof(Inst), cudaMemcpyHostToDevice, h->mem.st));
+  CK(cudaStreamSynchronize(h->mem.st));
+  if (h->solo) h->solo->dirty = true;
+  return rc;
 }
 
 int shell_energy(shell_handle *h, double out[4]) {

@@ -93,8 +93,12 @@ struct Inst {
   int32_t n_chunks;
   int32_t pcg_max_it, refine_max;
   int32_t nl_max;                // chord iterations per step of the exact backward Euler (<= 1: linearised step)
+  int32_t nl_newton;             // 1: the iterations use the Newton tangent (projected membrane Hessian at x_k)
+  int32_t nl_static;             // 1: quasi-static solve (Eq. 64): no inertia in the residual, eps_u limiter
   double dt, pcg_rtol, refine_rtol;
   double nl_rtol;                // chord stop: ||R(v_k)|| <= nl_rtol ||R(0)||
+  double nl_atol;                // or ||R(v_k)|| / dt <= nl_atol (static: ||f + f_ext|| <= nl_atol)
+  double nl_eps_u;               // static: largest nodal displacement of one iteration (0: no limit)
   double mu, lam;                // membrane Lame parameters (plane stress)
 
   // state (FP64, SoA [3][nv])
@@ -102,6 +106,7 @@ struct Inst {
   double *vprev;                 // velocity before the last committed step (warm-start extrapolation)
   double *vprev2, *vprev3;       // the two velocities before that (cubic extrapolation)
   double *xk;                    // [3][nv] chord iterate x + dt v_k, where the next forces are evaluated
+  double *vk;                    // [3][nv] the iterate v_k itself (quasi-static limiter)
   double *mass;                  // [nv]
   uint8_t *pinned;               // [nv]
 
@@ -116,6 +121,7 @@ struct Inst {
   double *m_D64;  float *m_D32;  // [3][nt] Dm^-1 = [[d0, d1], [0, d2]]
   double *m_G64;                 // [3][nt] rest Gram |A|^2, A.B, |B|^2 of edges A = X2-X1, B = X3-X1
   double *m_At64; float *m_At32; // [nt] area * thickness
+  double *m_T;                   // [10][nt] Newton tangent data (R0, R1, kappa, Q00, Q01, Q11), see store_tangent
 
   // edge stencils (edge hinge models)
   int32_t *e_idx;                // [4][ne] (x1, x2, x3, x4); x4 = -1 on clamped stencils
@@ -217,12 +223,12 @@ cudaError_t launch_matvec64(const Inst *d_inst, const Inst &h_inst, const double
                            cudaStream_t st);
 cudaError_t launch_pack_states(const Inst *d_insts, int n, const long long *d_offs, long long rows, double *d_x,
                                double *d_v, int unpack, cudaStream_t st);
-int solve_blocks_per_sm(int prec, int occ);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only
+int solve_blocks_per_sm(int prec, int occ);   // prec: 0 mixed, 1 FP64 only, 2 FP32-refinement only, 3 Newton
 int solve_max_clusters(int prec, int cluster);   // co-resident clusters of the solve kernel, 0 if unsupported
 constexpr int kCluster = 8;                      // cluster size of the batched solve launch (portable)
 int static_max_ctas();
-cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
-                               int n_steps, int chord_launches, InstStatus *h_status, int32_t *h_aborted,
-                               cudaStream_t st);
+cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int newton,
+                               int team_ctas, int n_steps, int chord_launches, InstStatus *h_status,
+                               int32_t *h_aborted, cudaStream_t st);
 
 }  // namespace shl

@@ -1,7 +1,8 @@
-// kernels_solve.cu -- persistent per-step solve: right-hand side, preconditioned conjugate gradients on the
-// constant matrix (Jacobi, or a smoothed-aggregation multigrid V-cycle with its damped-Jacobi sweeps folded
-// into the transfers and one dense operator for its coarse end), state update. One launch per step serves
-// every instance of a batch.
+// kernels_solve.cu -- persistent step kernel: per-stencil forces, right-hand side, preconditioned conjugate
+// gradients on the constant matrix (Jacobi, or a smoothed-aggregation multigrid V-cycle with its damped-Jacobi
+// sweeps folded into the transfers and one dense operator for its coarse end), state update. One launch per
+// step serves every instance of a batch; each team evaluates its own FP32 instance's stencils before its solve
+// (FP64 instances take their forces from the standalone force launch just before).
 //
 // Step (Section 5, Eq. 62-63, linearised): (M + dt^2 K) v' = M v + dt (f + f_ext); x' = x + dt v'.
 // Exact backward Euler (optional, per instance): the same launch repeated as a chord iteration, each with
@@ -34,6 +35,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "stencil_force.cuh"
 
 namespace shl {
 namespace {
@@ -485,7 +487,84 @@ __device__ __forceinline__ void staged_row64(const HaloDev &H, int blk, const D4
   }
 }
 
+// ------------------------------------------------------------------ Newton tangent
+// Row `row` of dt^2 (H - K_iso) u, summed over the triangles incident to the row's vertex: H_t is the membrane
+// Hessian of triangle t at the positions of its last force evaluation, projected to positive semi-definite
+// (tangent data m_T, see store_tangent), K_iso,t the constant isotropic block 2 (mu + lam) A t grad(phi_a) .
+// grad(phi_b) (x) I_3 the step matrix holds. Added to the step matrix's product, it gives the Newton matrix
+// M + dt^2 (K_b + sum_t H_t). With U = sum_b u_b g_b^T (3x2, g_b the hat gradients), A = R^T U, b = U^T n:
+//   y_a = A t [R Sigma + n (Q b)^T - 2 (mu + lam) U] g_a,
+//   Sigma = 2 mu sym(A) + lam tr(A) I + kappa (A_10 - A_01) [[0, -1], [1, 0]].
+// Pinned vertices have identity rows and columns in the step matrix: their rows get no correction and their
+// entries of u count as zero. u: gathered vector (AoS) of the product.
+template <typename R, typename G>
+__device__ __noinline__ void tangent_corr(const Inst &I, const G *u, int row, R &cx, R &cy, R &cz) {
+  cx = cy = cz = R(0);
+  if (I.pinned[row]) return;
+  const int nt = I.nt, kt = I.kt;
+  const R mu = R(I.mu), lam = R(I.lam), w2 = R(2) * (mu + lam);
+  const double *T = I.m_T;
+  v3<R> y = zero3<R>();
+  for (int q = I.vtx_ptr[row]; q < I.vtx_ptr[row + 1]; ++q) {
+    const int s = I.vtx_slot[q];
+    if (s >= nt * kt) continue;            // an edge stencil's slot
+    const int t = s / kt, j = s - t * kt;
+    if (j >= 3) continue;                  // a bending neighbour's slot
+    v3<R> uu[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int v = I.t_idx[a * nt + t];
+      const G g = ldg4(u + v);
+      uu[a] = I.pinned[v] ? zero3<R>() : v3<R>{R(g.x), R(g.y), R(g.z)};
+    }
+    const R p = R(I.m_D64[t]), qd = R(I.m_D64[nt + t]), r = R(I.m_D64[2 * nt + t]), At = R(I.m_At64[t]);
+    const v3<R> du = uu[1] - uu[0], dv = uu[2] - uu[0];
+    const v3<R> U0 = p * du, U1 = qd * du + r * dv;
+    const v3<R> R0 = {R(T[t]), R(T[nt + t]), R(T[2 * nt + t])};
+    const v3<R> R1 = {R(T[3 * nt + t]), R(T[4 * nt + t]), R(T[5 * nt + t])};
+    const R kap = R(T[6 * nt + t]), Q00 = R(T[7 * nt + t]), Q01 = R(T[8 * nt + t]), Q11 = R(T[9 * nt + t]);
+    const v3<R> n = cross(R0, R1);
+    const R A00 = dot(R0, U0), A01 = dot(R0, U1), A10 = dot(R1, U0), A11 = dot(R1, U1);
+    const R b0 = dot(n, U0), b1 = dot(n, U1);
+    const R trA = A00 + A11, wv = A10 - A01, sy = mu * (A01 + A10);
+    const R S00 = R(2) * mu * A00 + lam * trA, S11 = R(2) * mu * A11 + lam * trA;
+    const R S01 = sy - kap * wv, S10 = sy + kap * wv;
+    const R Qb0 = Q00 * b0 + Q01 * b1, Qb1 = Q01 * b0 + Q11 * b1;
+    const v3<R> P0 = S00 * R0 + S10 * R1 + Qb0 * n - w2 * U0;
+    const v3<R> P1 = S01 * R0 + S11 * R1 + Qb1 * n - w2 * U1;
+    const v3<R> H0 = At * (p * P0 + qd * P1);
+    const v3<R> H1 = (At * r) * P1;
+    if (j == 0)
+      y = y - (H0 + H1);
+    else if (j == 1)
+      y = y + H0;
+    else
+      y = y + H1;
+  }
+  const R dt2 = R(I.dt * I.dt);
+  cx = dt2 * y.x;
+  cy = dt2 * y.y;
+  cz = dt2 * y.z;
+}
+
 // ------------------------------------------------------------------ phases
+// Per-stencil forces of the instance at the positions of this launch (x, or the chord iterate xk of exact
+// backward Euler), in the instance's precision, written to its contribution slots (one writer per slot). The
+// team's CTAs take 256-stencil chunks of the combined list (triangles, then edge stencils) round robin; the
+// right-hand side reads the slots after the next team barrier.
+template <typename R, bool NT>
+__device__ void phase_forces(const Inst &I, const Team &tm) {
+  const Data<R> D(I, tm.chord_k > 0 ? I.xk : I.x);
+  const int ns = I.nt + I.ne;
+  for (int c = tm.rank; c * kBlock < ns; c += tm.size) {
+    const int s = c * kBlock + (int)threadIdx.x;
+    if (s < I.nt)
+      tri_stencil<R, NT>(I, D, s, false);
+    else if (s < ns)
+      edge_stencil<R>(I, D, s - I.nt, false);
+  }
+}
+
 #define ROWS_BEGIN(I, tm)                                                                 \
   for (int ch = (tm).rank; ch < (I).n_chunks; ch += (tm).size) {                        \
     for (int rr = 0; rr < (I).rows_per_thread; ++rr) {                                  \
@@ -501,7 +580,7 @@ __device__ __forceinline__ void staged_row64(const HaloDev &H, int blk, const D4
 // Chord iteration k > 0 of the exact backward-Euler step (forces at x + dt v_k, v_k in sol and g64):
 // b = M v + dt (f + f_ext) + (A - M) v_k, warm start v_k kept, so that the first residual b - A v_k is
 // -R(v_k), the backward-Euler residual, and the solve gives v_{k+1} = v_k - A^-1 R(v_k).
-template <typename RC>
+template <typename RC, bool NT>
 __device__ void phase_rhs(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   const bool chord = tm.chord_k > 0;
@@ -514,29 +593,42 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
       if (row >= nv) continue;
       double f[3] = {0.0, 0.0, 0.0};
       for (int q = I.vtx_ptr[row]; q < I.vtx_ptr[row + 1]; ++q) {
-        const size_t s = (size_t)I.vtx_slot[q];
-        f[0] += double(con[3 * s]);
-        f[1] += double(con[3 * s + 1]);
-        f[2] += double(con[3 * s + 2]);
+        const size_t s = (size_t)I.vtx_slot[q];   // slots written by the team's force phase: coherent loads
+        f[0] += double(__ldcg(con + 3 * s));
+        f[1] += double(__ldcg(con + 3 * s + 1));
+        f[2] += double(__ldcg(con + 3 * s + 2));
       }
       const bool pin = I.pinned[row] != 0;
       const double m = I.mass[row];
       double av[3] = {0.0, 0.0, 0.0};
-      if (chord) spmv_row(I, I.val64, reinterpret_cast<const D4 *>(I.g64), row, av[0], av[1], av[2]);
+      if (chord) {
+        const D4 *vk = reinterpret_cast<const D4 *>(I.g64);
+        spmv_row(I, I.val64, vk, row, av[0], av[1], av[2]);
+        if constexpr (NT) {
+          if (I.nl_newton) {
+            double cx, cy, cz;
+            tangent_corr<double, D4>(I, vk, row, cx, cy, cz);
+            av[0] += cx;
+            av[1] += cy;
+            av[2] += cz;
+          }
+        }
+      }
       double sv[3];
       for (int c = 0; c < 3; ++c) {
         const double v = I.v[c * nv + row];
-        double b = m * v + I.dt * (f[c] + I.fext[c * nv + row]);
-        if (chord) b += av[c] - m * I.sol[c * nv + row];
+        // quasi-static: b = dt (f + f_ext) + J v_k, so that b - J v_k = dt (f + f_ext), the residual of Eq. 64
+        double b = (I.nl_static ? 0.0 : m * v) + I.dt * (f[c] + I.fext[c * nv + row]);
+        if (chord) b += av[c] - (I.nl_static ? 0.0 : m * I.sol[c * nv + row]);
         if (pin) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
         // initial guess: cubic extrapolation of the last four velocities, 4 (v + v_prev2) - 6 v_prev - v_prev3
         // (v_prev, v_prev2, v_prev3: the velocities before the last three committed steps; setting a state
-        // leaves them, as they only shape the initial guess)
+        // leaves them, as they only shape the initial guess); zero for the quasi-static solve
         if (!chord) {
           const int k = c * nv + row;
-          sv[c] = pin ? 0.0 : 4.0 * (v + I.vprev2[k]) - 6.0 * I.vprev[k] - I.vprev3[k];
+          sv[c] = (pin || I.nl_static) ? 0.0 : 4.0 * (v + I.vprev2[k]) - 6.0 * I.vprev[k] - I.vprev3[k];
           I.sol[c * nv + row] = sv[c];
         }
       }
@@ -550,7 +642,7 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
 // FP64 residual r64 = b - A64 sol; returns partial ||r64||^2. If R is float also prepares the inner CG:
 // r32 = r64, xs = 0 (FP64), g32 = D32^-1 r32. If R is double: r = r64 (in place), sol unchanged, g = D^-1 r.
 // Multigrid: also the first V-cycle's level-0 pre-smoothing from zero, b0 = r, x0 = omega D^-1 r (row-local).
-template <typename R>
+template <typename R, bool NT>
 __device__ void phase_resid(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   const bool amg = I.amg_levels > 0;
@@ -577,6 +669,15 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
       } else {
         if (row >= nv) continue;
         spmv_row(I, I.val64, g64, row, ax, ay, az);
+      }
+      if constexpr (NT) {
+        if (I.nl_newton) {
+          double cx, cy, cz;
+          tangent_corr<double, D4>(I, g64, row, cx, cy, cz);
+          ax += cx;
+          ay += cy;
+          az += cz;
+        }
       }
       const double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
       I.r64[row] = r0;
@@ -606,7 +707,7 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
 }
 
 // w = A u (u = g); partials (r,u), (w,u), (r,r)
-template <typename R>
+template <typename R, bool NT>
 __device__ void phase_spmv(const Inst &I, const Team &tm) {
   const int nv = I.nv;
   const R *val = Vec<R>::val(I);
@@ -637,6 +738,15 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
         if (row >= nv) continue;
         spmv_row(I, val, g, row, ax, ay, az);
         u = ldg4(g + row);
+      }
+      if constexpr (NT) {
+        if (I.nl_newton) {
+          R cx, cy, cz;
+          tangent_corr<R, typename Vec<R>::G>(I, g, row, cx, cy, cz);
+          ax += cx;
+          ay += cy;
+          az += cz;
+        }
       }
       w[row] = ax;
       w[nv + row] = ay;
@@ -1247,11 +1357,11 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
 // Chronopoulos-Gear PCG iterations on A x = r0, given r (initial residual), x (initial guess) and
 // g = D^-1 r. Stops when (r,r) <= tol2 (absolute). Returns iterations (>= 0), -1 on cap, -2 on abort,
 // -3 on a non-finite reduction.
-template <typename R>
+template <typename R, bool NT>
 __device__ int cg_loop(const Inst &I, Team &tm, double *x, double tol2, int max_it, double *rho_out) {
   if (!team_sync(tm)) return -2;
   if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
-  phase_spmv<R>(I, tm);
+  phase_spmv<R, NT>(I, tm);
   if (!team_sync(tm)) return -2;
   double red[3];
   team_reduce(I, tm, red);
@@ -1265,7 +1375,7 @@ __device__ int cg_loop(const Inst &I, Team &tm, double *x, double tol2, int max_
     phase_update<R>(I, tm, R(alpha), R(beta), first, x, alpha);
     if (!team_sync(tm)) return -2;
     if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
-    phase_spmv<R>(I, tm);
+    phase_spmv<R, NT>(I, tm);
     if (!team_sync(tm)) return -2;
     team_reduce(I, tm, red);
     const double gn = red[0], dn = red[1];
@@ -1297,34 +1407,104 @@ __device__ void phase_accumulate(const Inst &I, const Team &tm) {
   ROWS_END
 }
 
-// v_prev3 = v_prev2; v_prev2 = v_prev; v_prev = v; v = sol; x += dt v
+// v_prev3 = v_prev2; v_prev2 = v_prev; v_prev = v; v = sol; x += dt v. Quasi-static solve: x += dt sol and the
+// velocity and its history are zero (the equilibrium is at rest).
 __device__ void phase_commit(const Inst &I, const Team &tm) {
   const int nv = I.nv;
+  const bool st = I.nl_static != 0;
   ROWS_BEGIN(I, tm)
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
     const double v = I.sol[k];
-    I.vprev3[k] = I.vprev2[k];
-    I.vprev2[k] = I.vprev[k];
-    I.vprev[k] = I.v[k];
-    I.v[k] = v;
+    I.vprev3[k] = st ? 0.0 : I.vprev2[k];
+    I.vprev2[k] = st ? 0.0 : I.vprev[k];
+    I.vprev[k] = st ? 0.0 : I.v[k];
+    I.v[k] = st ? 0.0 : v;
     I.x[k] += I.dt * v;
   }
   ROWS_END
 }
 
-// hand-off to the next chord iteration: xk = x + dt sol (where the next forces are evaluated), g64 = sol
-__device__ void phase_chord(const Inst &I, const Team &tm) {
+// Largest |sol - v_k| over the instance's rows and components (v_k = 0 at the first iteration): per-chunk
+// maxima (warp shuffles, then the warps), then every CTA takes the maximum of all chunks (order-independent).
+// Returns false on abort.
+__device__ bool team_max_step(const Inst &I, Team &tm, double *out) {
+  __shared__ double wmax[kBlock / 32];
+  __shared__ double res;
+  const int nv = I.nv, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool first = tm.chord_k == 0;
+  for (int ch = tm.rank; ch < I.n_chunks; ch += tm.size) {
+    double mx = 0.0;
+    for (int rr = 0; rr < I.rows_per_thread; ++rr) {
+      const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
+      if (row >= nv) continue;
+      for (int c = 0; c < 3; ++c) {
+        const int k = c * nv + row;
+        mx = fmax(mx, fabs(I.sol[k] - (first ? 0.0 : I.vk[k])));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = wmax[0];
+      for (int w = 1; w < kBlock / 32; ++w) m = fmax(m, wmax[w]);
+      part_of(I, tm, ch)[0] = m;
+    }
+    __syncthreads();
+  }
+  if (!team_sync(tm)) return false;
+  const double *part = I.part + 4 * (size_t)tm.bank * I.n_chunks;
+  tm.bank ^= 1;
+  if (threadIdx.x < 32) {
+    double m = 0.0;
+    for (int c = threadIdx.x; c < I.n_chunks; c += 32) m = fmax(m, __ldcg(part + 4 * c));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) res = m;
+  }
+  __syncthreads();
+  *out = res;
+  return true;
+}
+
+// hand-off to the next iteration: the new iterate v_{k+1} = sol, or with the quasi-static limiter
+// v_k + alpha (sol - v_k); sol = vk = g64 = v_{k+1}, xk = x + dt v_{k+1} (where the next forces are evaluated)
+__device__ void phase_chord(const Inst &I, const Team &tm, double alpha, bool limit) {
   const int nv = I.nv;
+  const bool first = tm.chord_k == 0;
   ROWS_BEGIN(I, tm)
   double sv[3];
   for (int c = 0; c < 3; ++c) {
     const int k = c * nv + row;
     sv[c] = I.sol[k];
+    if (limit) {
+      const double v0 = first ? 0.0 : I.vk[k];
+      sv[c] = v0 + alpha * (sv[c] - v0);
+      I.sol[k] = sv[c];
+      I.vk[k] = sv[c];
+    }
     I.xk[k] = I.x[k] + I.dt * sv[c];
   }
   reinterpret_cast<D4 *>(I.g64)[row] = {sv[0], sv[1], sv[2], 0.0};
   ROWS_END
+}
+
+// stop test of an iteration of exact backward Euler or of the quasi-static solve: the current iterate's
+// residual r2 = ||R(v_k)||^2 meets nl_rtol ||R(0)|| (r0 = ||R(0)||^2) or dt nl_atol
+__device__ inline bool nl_done(const Inst &I, double r2, double r0) {
+  const double a = I.dt * I.nl_atol;
+  return r2 <= fmax(I.nl_rtol * I.nl_rtol * r0, a * a);
+}
+
+// squared floor of the linear solves of iterations k > 0: a tenth of the nonlinear target, since solving the
+// correction beyond what the stop test can see only costs iterations (and in FP32 with refinement runs into
+// the FP64 residual's rounding once ||R(v_k)|| is far below ||R(0)||)
+__device__ inline double nl_floor2(const Inst &I) {
+  const double r0 = __ldcg(&I.status->nl_r0);
+  const double a = I.dt * I.nl_atol;
+  return 0.01 * fmax(I.nl_rtol * I.nl_rtol * r0, a * a);
 }
 
 __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, int rounds, double rel) {
@@ -1358,7 +1538,7 @@ __device__ void set_status(const Inst &I, const Team &tm, int err, int iters, in
 // the launch, and its team mates may still pass the barrier before the commit (its last arrival completes
 // it), so every CTA checks the abort flag once before it writes the state; an abandoned launch then commits
 // nothing.
-__device__ bool finish_step(const Inst &I, const Team &tm, double bb, int iters, int rounds, double rel,
+__device__ bool finish_step(const Inst &I, Team &tm, double bb, int iters, int rounds, double rel,
                             bool done_early) {
   const int k = tm.chord_k;
   if (ld_volatile_i(tm.abort_flag)) return false;
@@ -1369,10 +1549,24 @@ __device__ bool finish_step(const Inst &I, const Team &tm, double bb, int iters,
   }
   const int solves = done_early ? k : k + 1;
   const bool last = done_early || solves >= I.nl_max;
-  if (last)
+  if (last && !done_early && I.nl_static) {
+    // quasi-static: the iteration limit came before the residual met eps_f; nothing is committed
+    set_status(I, tm, SHELL_ERR_NOT_CONVERGED, iters, rounds, rel);
+    return true;
+  }
+  if (last) {
     phase_commit(I, tm);
-  else
-    phase_chord(I, tm);
+  } else {
+    const bool limit = I.nl_static && I.nl_eps_u > 0.0;
+    double alpha = 1.0;
+    if (limit) {
+      double mx = 0.0;
+      if (!team_max_step(I, tm, &mx)) return false;
+      const double d = I.dt * mx;
+      alpha = d > I.nl_eps_u ? I.nl_eps_u / d : 1.0;
+    }
+    phase_chord(I, tm, alpha, limit);
+  }
   if (tm.rank == 0 && threadIdx.x == 0) {
     InstStatus *s = I.status;
     const long long step_pcg = (k == 0 ? 0 : s->nl_step_pcg) + iters;
@@ -1400,9 +1594,13 @@ __device__ bool finish_step(const Inst &I, const Team &tm, double bb, int iters,
 // returns false if the kernel must stop (abort). Chord iteration k > 0 of an exact backward-Euler step: the
 // first residual of the solve is the backward-Euler residual R(v_k); if it meets nl_rtol ||R(0)|| the step
 // commits v_k without solving, else the solve's tolerance refers to it.
+// FP64 instances get their forces from the standalone force launch before this one: the FP64 stencil needs
+// more registers than the FP64 solve variant has (126 at 2 CTAs per SM) and spilled there (a batch256 step of
+// the plain FP64 path took 16.6 instead of 14.6 ms with the phase inside).
+template <bool NT>
 __device__ bool solve_fp64(const Inst &I, Team &tm) {
   const int k = tm.chord_k;
-  phase_rhs<double>(I, tm);
+  phase_rhs<double, NT>(I, tm);
   if (!team_sync(tm)) return false;
   double red[3];
   team_reduce(I, tm, red);
@@ -1413,9 +1611,11 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
   }
   int iters = 0;
   double rho = 0.0, ref = bb;
-  bool early = false;
-  if (bb > 0.0) {
-    phase_resid<double>(I, tm);   // r = b - A sol, g = D^-1 r
+  // quasi-static, first iteration: the start (v_0 = 0, b = dt (f + f_ext)) may already be in equilibrium
+  bool early = k == 0 && I.nl_static && nl_done(I, bb, bb);
+  if (early) rho = bb;
+  if (bb > 0.0 && !early) {
+    phase_resid<double, NT>(I, tm);   // r = b - A sol, g = D^-1 r
     if (k > 0) {
       if (!team_sync(tm)) return false;
       team_reduce(I, tm, red);
@@ -1425,12 +1625,13 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
         return true;
       }
       const double r0 = __ldcg(&I.status->nl_r0);
-      early = rho <= I.nl_rtol * I.nl_rtol * r0;
+      early = nl_done(I, rho, r0);
       ref = early ? r0 : rho;
     }
     if (!early) {
-      const double tol2 = I.pcg_rtol * I.pcg_rtol * ref;
-      iters = cg_loop<double>(I, tm, I.sol, tol2, I.pcg_max_it, &rho);
+      // iteration k > 0: no need to solve below a tenth of the nonlinear target (inexact Newton)
+      const double tol2 = fmax(I.pcg_rtol * I.pcg_rtol * ref, k > 0 ? nl_floor2(I) : 0.0);
+      iters = cg_loop<double, NT>(I, tm, I.sol, tol2, I.pcg_max_it, &rho);
       if (iters == -2) return false;
       if (iters < 0) {
         set_status(I, tm, iters == -1 ? SHELL_ERR_NOT_CONVERGED : SHELL_ERR_NONFINITE, I.pcg_max_it, 0,
@@ -1438,18 +1639,23 @@ __device__ bool solve_fp64(const Inst &I, Team &tm) {
         return true;
       }
     }
-  } else {
+  } else if (!early) {
     // b = 0: the solution is v' = 0
     ROWS_BEGIN(I, tm)
     for (int c = 0; c < 3; ++c) I.sol[c * I.nv + row] = 0.0;
     ROWS_END
   }
-  return finish_step(I, tm, bb, iters, 0, ref > 0.0 ? sqrt(rho / ref) : 0.0, early);
+  // quasi-static: the reported residual is ||f + f_ext|| of the committed iterate
+  const double rel = (I.nl_static && early) ? sqrt(rho) / I.dt : (ref > 0.0 ? sqrt(rho / ref) : 0.0);
+  return finish_step(I, tm, bb, iters, 0, rel, early);
 }
 
+template <bool NT>
 __device__ bool solve_fp32r(const Inst &I, Team &tm) {
   const int k = tm.chord_k;
-  phase_rhs<float>(I, tm);
+  phase_forces<float, NT>(I, tm);
+  if (!team_sync(tm)) return false;
+  phase_rhs<float, NT>(I, tm);
   if (!team_sync(tm)) return false;
   double red[3];
   team_reduce(I, tm, red);
@@ -1465,7 +1671,7 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
     double tol_ref2 = I.refine_rtol * I.refine_rtol * bb;
     const double tin2 = I.pcg_rtol * I.pcg_rtol;
     for (;;) {
-      phase_resid<float>(I, tm);
+      phase_resid<float, NT>(I, tm);
       if (!team_sync(tm)) return false;
       team_reduce(I, tm, red);
       const double r2 = red[0];
@@ -1473,15 +1679,16 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
         set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, sqrt(r2 / ref));
         return true;
       }
-      if (rounds == 0 && k > 0) {   // chord: r2 = ||R(v_k)||^2
-        const double r0 = __ldcg(&I.status->nl_r0);
-        if (r2 <= I.nl_rtol * I.nl_rtol * r0) {
+      if (rounds == 0 && (k > 0 || I.nl_static)) {   // iteration k: r2 = ||R(v_k)||^2 (v_0 = 0 when static)
+        const double r0 = k > 0 ? __ldcg(&I.status->nl_r0) : r2;
+        if (nl_done(I, r2, r0)) {
           early = true;
-          rel = r0 > 0.0 ? sqrt(r2 / r0) : 0.0;
+          rel = I.nl_static ? sqrt(r2) / I.dt : (r0 > 0.0 ? sqrt(r2 / r0) : 0.0);
           break;
         }
         ref = r2;
-        tol_ref2 = I.refine_rtol * I.refine_rtol * r2;
+        // no need to solve below a tenth of the nonlinear target (inexact Newton)
+        tol_ref2 = fmax(I.refine_rtol * I.refine_rtol * r2, k > 0 ? nl_floor2(I) : 0.0);
       }
       rel = sqrt(r2 / ref);
       if (r2 <= tol_ref2) break;
@@ -1494,7 +1701,7 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
       // margin of 0.7 leaves room for the FP32 recurrence's drift), and at least a halving
       const double tol2 = fmin(fmax(tin2 * r2, 0.5 * tol_ref2), 0.25 * r2);
       double rho = 0.0;
-      const int it = cg_loop<float>(I, tm, reinterpret_cast<double *>(I.xs), tol2, I.pcg_max_it, &rho);
+      const int it = cg_loop<float, NT>(I, tm, reinterpret_cast<double *>(I.xs), tol2, I.pcg_max_it, &rho);
       if (it == -2) return false;
       if (it == -3) {
         set_status(I, tm, SHELL_ERR_NONFINITE, total, rounds, rel);
@@ -1516,7 +1723,9 @@ __device__ bool solve_fp32r(const Inst &I, Team &tm) {
 // PREC: 0 = instances of either precision, 1 = FP64 instances only, 2 = FP32-refinement instances only.
 // MINB: CTAs per SM the register allocation is bounded for (the FP32 variant is compiled for 3, 4 and 5;
 // more resident warps mean more loads in flight, at the price of register spills; the autotuner picks).
-template <int PREC, int MINB>
+// NT: the variant carries the Newton tangent (launched for batches with a Newton instance; the others run
+// variants without that code, whose register allocation it would otherwise burden).
+template <int PREC, int MINB, bool NT = false>
 __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__ insts, Sched sch) {
   Team tm;
   tm.team = sch.cta_team[blockIdx.x];
@@ -1544,9 +1753,9 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
     tm.t0 = gtimer();
     bool ok;
     if (PREC == 1 || (PREC == 0 && I.precision == SHELL_FP64))
-      ok = solve_fp64(I, tm);
+      ok = solve_fp64<NT>(I, tm);
     else
-      ok = solve_fp32r(I, tm);
+      ok = solve_fp32r<NT>(I, tm);
     if (!ok) return;
     // make this instance's final writes (status) ordered before the team moves on
     if (!team_sync(tm)) return;
@@ -1555,9 +1764,11 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
 
 }  // namespace
 
-// kernel of a precision mode and an occupancy variant (FP32: 3, 4 or 5 CTAs per SM; others: 2)
+// kernel of a precision mode and an occupancy variant (FP32: 3, 4 or 5 CTAs per SM; others: 2); prec 3: either
+// precision with the Newton tangent
 typedef void (*SolveFn)(const Inst *, Sched);
 static SolveFn solve_fn(int prec, int occ) {
+  if (prec == 3) return k_solve<0, 2, true>;
   if (prec == 2) {
     if (occ >= 5) return k_solve<2, 5>;
     if (occ == 4) return k_solve<2, 4>;
@@ -1577,7 +1788,7 @@ int solve_halo_cap(int prec, int occ) {
 }
 
 static cudaError_t prepare_solve_fn(int prec, int occ) {
-  static bool done[3][6];
+  static bool done[4][6];
   const int o = std::min(5, std::max(0, occ));
   if (done[prec][o]) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(solve_fn(prec, occ), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1686,9 +1897,9 @@ cudaError_t static_scratch_setup(unsigned int **out) {
 
 int static_max_ctas() { return kStaticMaxCtas; }
 
-cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int team_ctas,
-                               int n_steps, int chord_launches, InstStatus *h_status, int32_t *h_aborted,
-                               cudaStream_t st) {
+cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_tiles, int fp32, int newton,
+                               int team_ctas, int n_steps, int chord_launches, InstStatus *h_status,
+                               int32_t *h_aborted, cudaStream_t st) {
   unsigned int *base = nullptr;
   cudaError_t e = static_scratch_setup(&base);
   if (e != cudaSuccess) return e;
@@ -1728,9 +1939,9 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   if ((e = cudaMemsetAsync(sc.bar, 0, 4 * (kBarWords + 2), st)) != cudaSuccess) return e;
   for (int step = 0; step < n_steps; ++step) {
     for (int k = 0; k < chord_launches; ++k) {   // chord iterations of an exact backward-Euler step
-      if ((e = launch_forces(d_inst, d_tiles, n_tiles, 0, fp32, st, k)) != cudaSuccess) return e;
+      if (!fp32 && (e = launch_forces(d_inst, d_tiles, n_tiles, 0, 0, st, k)) != cudaSuccess) return e;
       sc.chord_k = k;
-      if ((e = launch_solve(d_inst, sc, team_ctas, fp32 ? 2 : 1, 3, st)) != cudaSuccess) return e;
+      if ((e = launch_solve(d_inst, sc, team_ctas, newton ? 3 : (fp32 ? 2 : 1), 3, st)) != cudaSuccess) return e;
     }
   }
   if ((e = launch_gather_status(d_inst, 1, status_out, sc.abort_flag, abort_out, st)) != cudaSuccess) return e;

@@ -4,7 +4,7 @@ Requests (meshes with a step count) arrive over time. A request is admitted as s
 budget holds its instance: its handle is created (host topology, multigrid set-up, the GPU precompute and
 assembly) on one of a few worker threads while the GPU steps the resident instances, then it joins the
 batch between two steps. Set-up is mostly host work, so several requests are built at once. Every
-step advances all resident instances in one force launch and one persistent solve launch. A request retires
+step advances all resident instances in one persistent launch. A request retires
 (and frees its device memory) after its last step. Each instance's result does not depend on the others
 in the batch (deterministic, team-size independent reductions), so a request gives the same state alone or
 in any mix.

@@ -39,3 +39,16 @@ def test_algorithmic_bytes_terms():
     # product (A - M) v_k, its right-hand side and the hand-off to the next iterate
     extra = bench.algorithmic_bytes(info, dict(stats, nl_iterations=3), 1) - bench.algorithmic_bytes(info, stats, 1)
     assert extra == 2 * 16 * 6000 + 2 * (12 * 19000 + (32 + 109 + 104) * 1000)
+
+
+def test_force_phase_bytes():
+    base = {"n_verts": 1000, "nnz": 19000, "n_slots": 6000, "vcycle_bytes": 0, "n_tris": 1900, "n_stencils": 2800}
+    stats = {"total_refine_rounds": 0, "total_pcg_iterations": 0}
+    tri = bench.algorithmic_bytes(dict(base, model="SP"), stats, 1) - bench.algorithmic_bytes(base, stats, 1)
+    assert tri == 244 * 1900 + 24 * 1000
+    edge = bench.algorithmic_bytes(dict(base, model="ES"), stats, 1) - bench.algorithmic_bytes(base, stats, 1)
+    assert edge == 88 * 1900 + 89 * 2800 + 24 * 1000
+    # every chord solve of an exact backward-Euler step evaluates the forces again
+    two = bench.algorithmic_bytes(dict(base, model="SP"), dict(stats, nl_iterations=2), 1)
+    one = bench.algorithmic_bytes(base, dict(stats, nl_iterations=2), 1)
+    assert two - one == 2 * (244 * 1900 + 24 * 1000)
