@@ -17,7 +17,11 @@ Printed line (one JSON object, rank 0):
              every instance from pinned memory, the step, device->host state),
   roofline   the step kernel (the only launch of a step): algorithmic bytes per launch / mean launch time vs
              measured HBM,
-  cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload.
+  cpu_baseline  the FP64 CPU oracle timed on a bounded sample of the same workload,
+  serving    a bounded run (10 s) of the serving workload: Poisson(200/s) arrivals of 1k-250k-vertex
+             requests admitted by a 120 GB budget, aggregate vertex-steps/s, step and queueing p50/p99,
+  static_cantilever  the quasi-static Newton-Raphson solve (Eq. 64) of the Section 6.1 cantilever for the
+             six models: Newton steps, w_tip and wall time, beside the paper's Table (context only).
 
 ``--impl reference`` times the FP64 CPU oracle alone on the same workload (bounded sample per step).
 Multi-GPU (torchrun): each rank runs its own batch of the same size (different seeds), no collective on the
@@ -56,6 +60,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-seconds-main", type=float, default=10.0,
+                    help="length of the bounded serving run whose summary the main line carries (0: none)")
+    ap.add_argument("--no-static", action="store_true", help="skip the quasi-static cantilever sub-record")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--budget-gb", type=float, default=120.0)
     ap.add_argument("--nonlinear", default=None,
@@ -100,18 +107,35 @@ def solve_source_hash(read=None):
     return h.hexdigest()
 
 
-def measured_traffic(workload_name):
-    """(DRAM bytes of one solve launch, algorithmic bytes of that same launch) from the committed ncu summary,
-    if it was taken on the current source of the solve kernel and this workload (else (None, None))."""
-    path = os.path.join(ROOT, "profiles", "k_solve_traffic.txt")
+def traffic_record(path=None):
+    """The committed ncu record of the step kernel's DRAM traffic (dict), or None."""
+    path = path or os.path.join(ROOT, "profiles", "k_solve_traffic.txt")
     try:
-        kv = dict(line.split(None, 1) for line in open(path) if line.strip() and not line.startswith("#"))
+        return {k: v.strip() for k, v in (line.split(None, 1) for line in open(path)
+                                          if line.strip() and not line.startswith("#"))}
     except Exception:
-        return None, None
-    if kv.get("source_sha1", "").strip() != solve_source_hash() or kv.get("workload", "").strip() != workload_name:
+        return None
+
+
+def measured_traffic(workload_name, record=None):
+    """(DRAM bytes of one step launch, algorithmic bytes of that same launch) from the committed ncu summary,
+    if it was taken on the current source of the step kernel and this workload (else (None, None))."""
+    kv = traffic_record() if record is None else record
+    if not kv or kv.get("source_sha1") != solve_source_hash() or kv.get("workload") != workload_name:
         return None, None
     algo = kv.get("algorithmic_bytes_of_captured_launch")
     return float(kv["traffic_bytes_per_launch"]), (float(algo) if algo else None)
+
+
+def scaled_traffic(algo_per_launch, record=None):
+    """DRAM traffic of a launch of this workload estimated from a capture of a smaller one of the same kind on
+    the current source: the capture's DRAM / algorithmic ratio times this launch's algorithmic bytes (traffic
+    grows with the units processed). Returns (bytes, ratio, captured workload) or (None, None, None)."""
+    kv = traffic_record() if record is None else record
+    if not kv or kv.get("source_sha1") != solve_source_hash() or not kv.get("algorithmic_bytes_of_captured_launch"):
+        return None, None, None
+    ratio = float(kv["traffic_bytes_per_launch"]) / float(kv["algorithmic_bytes_of_captured_launch"])
+    return ratio * algo_per_launch, ratio, kv.get("workload")
 
 
 def rank_seed(seed, rank):
@@ -307,6 +331,50 @@ def serve(args, gb, torch, dev, rank, world):
         emit(line)
 
 
+# the paper's Table (Section 6.1): w_tip and Newton iterations of the cantilever, context only (its membrane,
+# mesh split and free-edge treatment are not stated; ABAQUS S4R gives 6.012)
+PAPER_CANTILEVER = {"EP": (5.388, 61), "ES": (5.387, 61), "FP": (6.056, 68), "FS": (6.072, 68), "SP": (6.055, 67),
+                    "SS": (6.072, 67)}
+
+
+def static_record(gb):
+    """Quasi-static cantilever of Section 6.1 (17 x 3 nodes, end shear 4, eps_f = 1e-3, eps_u = 0.1) for the six
+    models on the GPU (FP64, Newton with the displacement limit, multigrid preconditioner): Newton steps, w_tip
+    and wall time per solve."""
+    import shellgen as sg
+    out = {}
+    for model in sg.MODELS:
+        sc = sg.cantilever(model)
+        # the multigrid preconditioner of the constant matrix halves the PCG iterations of the Newton solves
+        # here (0.65 instead of 0.96 s per solve with Jacobi)
+        h = gb.create_from_scenario(sc, precision="fp64", preconditioner="amg")
+        t0 = time.perf_counter()
+        st = gb.shell_solve_static(h, eps_f=1e-3, eps_u=0.1, max_iters=400)
+        wall = time.perf_counter() - t0
+        x, _ = gb.shell_get_state(h)
+        tip = sg.cantilever_tip(sc)
+        out[model] = {"w_tip": float(x[tip, 2] - sc.rest[tip, 2]), "newton_steps": st["nl_iterations"],
+                      "residual": st["rel_residual"], "wall_s": round(wall, 4),
+                      "paper_w_tip": PAPER_CANTILEVER[model][0], "paper_iterations": PAPER_CANTILEVER[model][1]}
+        gb.shell_destroy(h)
+    return out
+
+
+def serving_record(args, gb, torch, rank, seconds):
+    """A bounded run of the serving workload (Poisson 200/s arrivals of 1k-250k-vertex requests, 120 GB budget):
+    aggregate vertex-steps/s, per-step latency and queueing percentiles."""
+    import shellgen as sg
+    from paper_2502_10872_gb300.serving import Request, Server
+    arrivals = sg.serving_requests(int(200 * seconds) + 20, rate_hz=200.0, seed=rank_seed(args.seed, rank))
+    reqs = [Request(k, t, sc, sc.steps) for k, (t, sc) in enumerate(arrivals)]
+    srv = Server(budget_bytes=int(args.budget_gb * (1 << 30)), precision="fp32_refine")
+    rep = srv.run(reqs, max_wall_s=seconds)
+    srv.close()
+    summ = rep.summary()
+    summ["wall_limit_s"] = seconds
+    return summ
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -415,6 +483,11 @@ def main():
     # DRAM traffic of one steady-state launch from a committed ncu capture, with that launch's own
     # algorithmic bytes (its iteration counts differ a little from the timed steps' mean)
     traffic, traffic_algo = measured_traffic(args.workload)
+    traffic_note = "ncu capture of this workload" if traffic is not None else None
+    if traffic is None:
+        est, ratio, wl = scaled_traffic(algo / (K * max(1, int(args.nonlinear.split(",")[0]) if args.nonlinear else 1)))
+        if est is not None:
+            traffic, traffic_note = est, f"scaled from an ncu capture of {wl} (DRAM / algorithmic = {ratio:.3f})"
     # per step: one persistent launch (forces, right-hand side, solve, commit), per chord iteration
     lps = int(args.nonlinear.split(",")[0]) if args.nonlinear else 1
     lps = max(1, lps)
@@ -470,6 +543,13 @@ def main():
                "h2d_bytes_per_step": 48 * rows, "d2h_bytes_per_step": 48 * rows,
                "api": "shell_batch_set_states + shell_batch_step + shell_batch_get_states, pinned host buffers"}
 
+    gb.shell_batch_destroy(b32)
+    del h32
+    static = None if args.no_static else static_record(gb)
+    serving = None
+    if args.serve_seconds_main > 0:
+        serving = serving_record(args, gb, torch, rank, args.serve_seconds_main)
+
     cpu = None
     if rank == 0:
         v, sample, secs, cores = time_oracle(scs, args.cpu_seconds, workers=args.cpu_workers)
@@ -498,15 +578,17 @@ def main():
                    "mean_refine_rounds_per_step": float(np.mean(rounds))},
         "roofline": {"kernel": "k_solve", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "traffic_launch_algorithmic_bytes": traffic_algo,
+                     "traffic_source": traffic_note,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo / (K * lps), "mean_launch_ms": kern32[1] / (K * lps),
                      "phases": "forces, right-hand side, PCG with refinement, commit: one launch per step"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),
         "wall_s_timed": wall32,
+        "serving": serving,
+        "static_cantilever": static,
     }
     if rank == 0:
         emit(line)
-    gb.shell_batch_destroy(b32)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -52,3 +52,13 @@ def test_force_phase_bytes():
     two = bench.algorithmic_bytes(dict(base, model="SP"), dict(stats, nl_iterations=2), 1)
     one = bench.algorithmic_bytes(base, dict(stats, nl_iterations=2), 1)
     assert two - one == 2 * (244 * 1900 + 24 * 1000)
+
+
+def test_scaled_traffic_uses_the_capture_ratio_on_the_current_source():
+    rec = {"source_sha1": bench.solve_source_hash(), "workload": "batch128", "traffic_bytes_per_launch": "4.4e9",
+           "algorithmic_bytes_of_captured_launch": "4.0e9"}
+    est, ratio, wl = bench.scaled_traffic(8.0e9, record=rec)
+    assert wl == "batch128" and abs(ratio - 1.1) < 1e-12 and abs(est - 8.8e9) < 1.0
+    assert bench.measured_traffic("batch256", record=rec) == (None, None)
+    stale = dict(rec, source_sha1="0" * 40)
+    assert bench.scaled_traffic(8.0e9, record=stale) == (None, None, None)
