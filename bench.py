@@ -564,7 +564,7 @@ def main():
         "ms_per_step": t_max * 1000.0 / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "instances": len(scs), "vertices": V_total,
-                   "precision": "fp32_refine", "refine_rtol": 1e-8, "pcg_rtol_inner": 1e-6,
+                   "precision": "fp32_refine", "refine_rtol": 3e-7, "pcg_rtol_inner": 1e-6,
                    "l2": "inputs larger than L2 (batch working set > 129 MB)", "seed": args.seed,
                    "parallelism": f"instances per rank, {world} rank(s)"},
         "latency_ms": {"p50": p50, "p99": p99},

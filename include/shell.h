@@ -139,8 +139,8 @@ typedef struct shell_options {
 
 /* Solver options of the step (Section 5; the paper names no linear solver or tolerance, so these are this
  * library's). Fills defaults: dt 1e-2, FP64, pcg_rtol 0 and refine_rtol 0 (= the precision's default: 1e-13 for the
- * FP64 PCG, 1e-6 for the inner FP32 PCG, 1e-8 for the refinement: the FP32 force rounding, not the
- * solve, then bounds the error), pcg_max_it 20000, refine_max 20,
+ * FP64 PCG, 1e-6 for the inner FP32 PCG, 3e-7 for the refinement: at that target and below the FP32 force
+ * rounding, not the solve, bounds the error against FP64), pcg_max_it 20000, refine_max 20,
  * preconditioner AUTO. */
 void shell_default_options(shell_options *opt);
 
