@@ -306,6 +306,7 @@ int rebuild_tables(shell_batch *b) {
   std::sort(order.begin(), order.end(), [&](int a, int c) { return work[a] > work[c]; });
   std::vector<int> team_size, team_of(n, -1);
   std::vector<std::vector<int>> team_inst;
+  std::vector<int32_t> queue;   // one-CTA instances taken dynamically (flat policy)
   int used = 0;
   auto t_of = [&](int k, int c) { return work[k] * factor(k, c); };
   if (CS) {
@@ -383,10 +384,15 @@ int rebuild_tables(shell_batch *b) {
         used += team_size.back();
       }
     }
-    for (auto &bl : bins) {
-      for (int k : bl) team_of[k] = (int)team_size.size();
+    // the one-CTA instances are not bound to the bins the plan sized: they form a queue in decreasing work,
+    // served by one-CTA workers (every CTA the multi-CTA teams leave, at least as many as the bins) and by the
+    // CTAs of the multi-CTA teams once their instance is done, so that the estimates' errors even out
+    for (int k : order)
+      if (t_of(k, 1) <= hi) queue.push_back(k);
+    const int workers = queue.empty() ? 0 : std::max((int)bins.size(), G - used);
+    for (int w = 0; w < workers; ++w) {
       team_size.push_back(1);
-      team_inst.push_back(bl);
+      team_inst.push_back({});
       used += 1;
     }
   }
@@ -441,6 +447,8 @@ int rebuild_tables(shell_batch *b) {
     b->sched.bar = C.take<unsigned int>((size_t)kBarWords * n_teams);
     b->sched.abort_flag = C.take<int32_t>(1);
     b->sched.cluster_ok = C.take<int32_t>(grid / (CS ? CS : 1) + 1);
+    b->sched.queue = C.take<int32_t>(std::max<size_t>(1, queue.size()));
+    b->sched.queue_ctr = C.take<unsigned int>(1);
     b->d_status_out = C.take<InstStatus>(n);
     b->d_abort_out = C.take<int32_t>(1);
     b->d_offs = C.take<long long>(n + 1);
@@ -468,6 +476,9 @@ int rebuild_tables(shell_batch *b) {
   CK(cudaMemcpyAsync(b->sched.team_size, tsize.data(), 4 * n_teams, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_ptr, tptr.data(), 4 * (n_teams + 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(b->sched.team_list, tlist.data(), 4 * tlist.size(), cudaMemcpyHostToDevice, st));
+  b->sched.n_queue = (int32_t)queue.size();
+  if (!queue.empty())
+    CK(cudaMemcpyAsync(b->sched.queue, queue.data(), 4 * queue.size(), cudaMemcpyHostToDevice, st));
   std::vector<long long> offs(n + 1, 0);
   for (int k = 0; k < n; ++k) offs[k + 1] = offs[k] + b->slots[b->active[k]]->nv;
   b->rows_total = offs[n];
@@ -485,6 +496,10 @@ int rebuild_tables(shell_batch *b) {
 cudaError_t solve_launch(shell_batch *b, cudaStream_t st, int chord_k) {
   b->sched.chord_k = chord_k;
   b->sched.wait_ns = b->wait_ns;
+  if (b->sched.n_queue > 0) {   // the queue of one-CTA instances starts at its head in every launch
+    cudaError_t e = cudaMemsetAsync(b->sched.queue_ctr, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+  }
   cudaError_t e = launch_solve(b->d_insts, b->sched, b->grid, b->prec, b->occ_launch, st);
   if (e != cudaSuccess && b->sched.cluster > 0) {
     cudaGetLastError();

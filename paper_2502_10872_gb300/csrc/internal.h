@@ -201,6 +201,11 @@ struct Sched {
   int32_t halo_cap;      // vector entries the launch's dynamic shared memory stages (set by launch_solve)
   int32_t chord_k;       // chord iteration of the step this launch performs (0: the first, or the only one)
   unsigned long long wait_ns;  // bound of a team-barrier wait (ns); past it the CTA raises the abort flag
+  // instances solved by one CTA each, taken in this order by whichever CTA is free: the single-CTA teams, and
+  // the CTAs of multi-CTA teams once their own list is done (queue_ctr is zeroed before every launch)
+  int32_t *queue;
+  unsigned int *queue_ctr;
+  int32_t n_queue;
 };
 
 // ---------------------------------------------------------------- launchers (defined in .cu files)

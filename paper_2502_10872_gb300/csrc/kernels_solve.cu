@@ -1746,8 +1746,32 @@ __global__ void __launch_bounds__(kBlock, MINB) k_solve(const Inst *__restrict__
     tm.mode = (tm.size == sch.cluster) ? 2 : 3;
   else
     tm.mode = 1;
-  for (int q = sch.team_ptr[tm.team]; q < sch.team_ptr[tm.team + 1]; ++q) {
-    const Inst &I = insts[sch.team_list[q]];
+  // The team's own list first, then the shared queue of one-CTA instances, which every CTA serves once its
+  // team's list is done (results do not depend on which CTA solves an instance). Both feed the same solver
+  // call: a second, separately inlined call with the team size known to be 1 compiled to different rounding.
+  __shared__ int s_q;
+  const int q_end = sch.team_ptr[tm.team + 1];
+  int q = sch.team_ptr[tm.team];
+  const int team_size = tm.size, team_rank = tm.rank, team_mode = tm.mode;
+  bool in_queue = false;
+  for (;;) {
+    int idx;
+    if (q < q_end) {
+      idx = sch.team_list[q++];
+    } else {
+      if (sch.n_queue <= 0) break;
+      if (threadIdx.x == 0) s_q = ld_volatile_i(tm.abort_flag) ? sch.n_queue : (int)atomicAdd(sch.queue_ctr, 1u);
+      __syncthreads();
+      const int qq = s_q;
+      __syncthreads();
+      if (qq >= sch.n_queue) break;
+      idx = sch.queue[qq];
+      in_queue = true;
+    }
+    tm.size = in_queue ? 1 : team_size;
+    tm.rank = in_queue ? 0 : team_rank;
+    tm.mode = in_queue ? 0 : team_mode;
+    const Inst &I = insts[idx];
     if (I.status->err != SHELL_OK) continue;
     if (sch.chord_k > 0 && !(I.status->nl_flags & 1)) continue;   // no chord iteration in progress
     tm.t0 = gtimer();
@@ -1920,6 +1944,9 @@ cudaError_t launch_step_static(const Inst *d_inst, const Tile *d_tiles, int n_ti
   sc.cluster = 0;
   sc.cluster_ok = nullptr;
   sc.wait_ns = (unsigned long long)kMaxTeamWaitMs * 1000000ull;
+  sc.queue = nullptr;
+  sc.queue_ctr = nullptr;
+  sc.n_queue = 0;
   static thread_local int32_t host_tab[2 * kStaticMaxCtas + 4];
   for (int c = 0; c < team_ctas; ++c) {
     host_tab[c] = 0;
