@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--nonlinear", default=None,
                     help="K,RTOL: exact backward Euler (chord iteration, up to K solves per step, stop at "
                          "||R|| <= RTOL ||R(0)||) instead of the linearised step, for every instance")
+    ap.add_argument("--newton", action="store_true",
+                    help="with --nonlinear: Newton iterations (tangent of the corotated membrane) instead of the "
+                         "chord iteration")
     ap.add_argument("--launch", default=None,
                     help="CTAS_PER_SM,SHARE,CLUSTERS: apply this solve-launch shape to the FP32 batch instead of "
                          "autotuning (e.g. the shape a plain run chose, for a profiler run whose timings would "
@@ -435,6 +438,8 @@ def main():
             kk, rt = args.nonlinear.split(",")
             for h in hs:
                 gb.shell_set_nonlinear(h, int(kk), float(rt))
+                if args.newton:
+                    gb.shell_set_newton(h, True)
         b = gb.shell_batch_create(1 << 50)
         for h in hs:
             gb.shell_batch_admit(b, h)
@@ -571,8 +576,8 @@ def main():
         "autotune": tuned,
         "fp64": fp64, "accuracy": acc,
         "integrator": ("linearised backward Euler" if not args.nonlinear else
-                       f"exact backward Euler (chord iteration, K,rtol = {args.nonlinear}); mean chord "
-                       f"iterations in the last step {float(np.mean(chord)):.2f}"),
+                       f"exact backward Euler ({'Newton' if args.newton else 'chord'} iteration, K,rtol = "
+                       f"{args.nonlinear}); mean iterations in the last step {float(np.mean(chord)):.2f}"),
         "solver": {"mean_inner_iterations_per_step": float(np.mean(iters)),
                    "max_inner_iterations_per_step": float(np.max(iters)),
                    "mean_refine_rounds_per_step": float(np.mean(rounds))},

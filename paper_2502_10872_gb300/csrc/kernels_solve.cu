@@ -592,11 +592,23 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
       const int row = (ch * I.rows_per_thread + rr) * kBlock + (int)threadIdx.x;
       if (row >= nv) continue;
       double f[3] = {0.0, 0.0, 0.0};
-      for (int q = I.vtx_ptr[row]; q < I.vtx_ptr[row + 1]; ++q) {
-        const size_t s = (size_t)I.vtx_slot[q];   // slots written by the team's force phase: coherent loads
-        f[0] += double(__ldcg(con + 3 * s));
-        f[1] += double(__ldcg(con + 3 * s + 1));
-        f[2] += double(__ldcg(con + 3 * s + 2));
+      // the vertex's slots in their fixed order, four per round: the slot indices, then their contributions
+      // (written by the team's force phase: coherent loads), are in flight together
+      const int q1 = I.vtx_ptr[row + 1];
+      for (int q = I.vtx_ptr[row]; q < q1; q += 4) {
+        size_t sl[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sl[j] = q + j < q1 ? (size_t)I.vtx_slot[q + j] : 0;
+        RC cv[4][3];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) cv[j][c] = q + j < q1 ? __ldcg(con + 3 * sl[j] + c) : RC(0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (q + j < q1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] += double(cv[j][c]);
       }
       const bool pin = I.pinned[row] != 0;
       const double m = I.mass[row];
