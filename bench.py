@@ -241,6 +241,12 @@ def force_bytes(info):
     return 244.0 * T + 24.0 * V
 
 
+def algorithmic_bytes_without_vcycle(info, stats, steps):
+    """The same byte model without the multigrid cycle's operator and vector bytes: the per-iteration count of
+    a Jacobi-preconditioned PCG (values, indices and the five vectors), for comparison with that model."""
+    return algorithmic_bytes(dict(info, vcycle_bytes=0), stats, steps)
+
+
 def algorithmic_bytes(info, stats, steps):
     """Compulsory DRAM bytes of the step kernel (FP32 + refinement) for ``steps`` steps of one instance.
 
@@ -482,8 +488,10 @@ def main():
     # ---- roofline of the solve kernel
     infos = [dict(gb.shell_info(h), model=sc.model) for h, sc in zip(h32, scs)]
     algo = sum(algorithmic_bytes(infos[k], stats32[k], K) for k in range(len(h32)))
+    algo_nv = sum(algorithmic_bytes_without_vcycle(infos[k], stats32[k], K) for k in range(len(h32)))
     solve_s = kern32[1] / 1000.0
     achieved = algo / K / (solve_s / K) / 1e9
+    achieved_nv = algo_nv / K / (solve_s / K) / 1e9
     peak, peak_kind = load_peaks()
     # DRAM traffic of one steady-state launch from a committed ncu capture, with that launch's own
     # algorithmic bytes (its iteration counts differ a little from the timed steps' mean)
@@ -586,7 +594,10 @@ def main():
                      "traffic_source": traffic_note,
                      "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": algo / (K * lps), "mean_launch_ms": kern32[1] / (K * lps),
-                     "phases": "forces, right-hand side, PCG with refinement, commit: one launch per step"},
+                     "phases": "forces, right-hand side, PCG with refinement, commit: one launch per step",
+                     "frac_without_vcycle_bytes": achieved_nv / peak,
+                     "frac_without_vcycle_note": "the same launch time over the bytes of the model without the "
+                                                 "multigrid cycle (a Jacobi-PCG iteration's count)"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk.summary(),
         "wall_s_timed": wall32,
         "serving": serving,

@@ -20,21 +20,30 @@ bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, cons
   std::vector<std::vector<int32_t>> lists(n_blocks);
   H.own.assign(n_blocks, 0);
   H.c16.assign(sl_col.size(), 0);
+  // loc[c]: local index of column c in the current block's list, -1 outside it (reset after each block), so
+  // the distinct columns are collected in one pass and only they are sorted
+  std::vector<int32_t> loc(std::max(n_cols, n_rows), -1);
   std::vector<int32_t> list;
+  auto mark = [&](int c) {
+    if (loc[c] < 0) {
+      loc[c] = 0;
+      list.push_back(c);
+    }
+  };
   for (int b = 0; b < n_blocks; ++b) {
     const int r0 = b * rows_blk, r1 = std::min(n_rows, r0 + rows_blk);
     list.clear();
     for (int r = r0; r < r1; ++r) {
       const int len = row_ptr[r + 1] - row_ptr[r];
-      for (int k = 0; k < len; ++k) list.push_back(sl_col[pos_of(r, k)]);
-      if (square) list.push_back(r);
+      for (int k = 0; k < len; ++k) mark(sl_col[pos_of(r, k)]);
+      if (square) mark(r);
     }
-    if (list.empty()) list.push_back(0);
+    if (list.empty()) mark(0);
     std::sort(list.begin(), list.end());
-    list.erase(std::unique(list.begin(), list.end()), list.end());
     if (list.size() > 65535) return false;
+    for (size_t i = 0; i < list.size(); ++i) loc[list[i]] = (int32_t)i;
     H.max = std::max(H.max, (int)list.size());
-    const int own = square ? (int)(std::lower_bound(list.begin(), list.end(), r0) - list.begin()) : 0;
+    const int own = square ? loc[r0] : 0;
     H.own[b] = own;
     for (int r = r0; r < r1; ++r) {
       const int s = r / rows_slice;
@@ -42,14 +51,10 @@ bool build_halo(int n_rows, int n_cols, const std::vector<int32_t> &sl_ptr, cons
       const int w = (sl_ptr[s + 1] - sl_ptr[s]) / 32 * lanes;   // stored entries of the row, padding included
       for (int k = 0; k < w; ++k) {
         const int pos = pos_of(r, k);
-        int loc;
-        if (k < len)
-          loc = (int)(std::lower_bound(list.begin(), list.end(), sl_col[pos]) - list.begin());
-        else
-          loc = square ? own + (r - r0) : 0;
-        H.c16[pos] = (uint16_t)loc;
+        H.c16[pos] = (uint16_t)(k < len ? loc[sl_col[pos]] : (square ? own + (r - r0) : 0));
       }
     }
+    for (int c : list) loc[c] = -1;
     lists[b] = list;
   }
   H.col.assign((size_t)n_blocks * H.max, 0);

@@ -68,6 +68,26 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     auto it = std::lower_bound(de.begin(), de.end(), key, [](const DirEdge &x, uint64_t k) { return x.key < k; });
     return (it != de.end() && it->key == key) ? &*it : nullptr;
   };
+  // twin[i]: index in de of the reverse of directed edge i (-1 on the boundary), by one merge of de with its
+  // reversed keys in sorted order; at[3 t + k]: index in de of triangle t's edge k. Lookups of the hot loops
+  // below then cost O(1) instead of a binary search over all directed edges.
+  std::vector<int32_t> twin(de.size(), -1), at(de.size());
+  {
+    std::vector<std::pair<uint64_t, int32_t>> rev(de.size());
+    for (size_t i = 0; i < de.size(); ++i) {
+      const uint64_t p = de[i].key / N, q = de[i].key % N;
+      rev[i] = {q * N + p, (int32_t)i};
+      const int32_t *v = tris + 3 * (size_t)de[i].tri;
+      const int k = (v[0] == (int)p) ? 0 : (v[1] == (int)p) ? 1 : 2;
+      at[3 * (size_t)de[i].tri + k] = (int32_t)i;
+    }
+    std::sort(rev.begin(), rev.end());
+    size_t j = 0;
+    for (const auto &pr : rev) {
+      while (j < de.size() && de[j].key < pr.first) ++j;
+      if (j < de.size() && de[j].key == pr.first) twin[pr.second] = (int32_t)j;
+    }
+  }
 
   // ---- clamped boundary edges (undirected keys)
   std::vector<uint64_t> clamp_keys;
@@ -83,12 +103,13 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     uint64_t k = (uint64_t)std::min(a, b) * N + std::max(a, b);
     return std::binary_search(clamp_keys.begin(), clamp_keys.end(), k);
   };
-  // neighbour across directed edge a->b of a triangle, and the hinge condition
-  auto hinge = [&](int a, int b, int *nb) -> uint8_t {
-    const DirEdge *tw = find((uint64_t)b * N + a);
-    if (tw) { *nb = tw->opp; return 0; }
+  // neighbour across edge k (v[k] -> v[k+1]) of triangle t, and the hinge condition
+  auto hinge = [&](int t, int k, int *nb) -> uint8_t {
+    const int32_t tw = twin[at[3 * (size_t)t + k]];
+    if (tw >= 0) { *nb = de[tw].opp; return 0; }
     *nb = -1;
-    return is_clamped(a, b) ? 2 : 1;
+    const int32_t *v = tris + 3 * (size_t)t;
+    return is_clamped(v[k], v[(k + 1) % 3]) ? 2 : 1;
   };
 
   // ---- triangle stencils
@@ -97,17 +118,20 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
   for (int t = 0; t < nt; ++t) {
     int v[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
     int dummy;
+    int r0 = 0;   // the rotation: edge r0 of the input triangle becomes edge 1-2
     for (int rot = 0; rot < 3; ++rot) {
-      if (hinge(v[rot], v[(rot + 1) % 3], &dummy) == 1) {
+      if (hinge(t, rot, &dummy) == 1) {
         int w[3] = {v[rot], v[(rot + 1) % 3], v[(rot + 2) % 3]};
         std::memcpy(v, w, sizeof(v));
+        r0 = rot;
         break;
       }
     }
+    // edges of the rotated triangle: 2-3, 3-1 and 1-2 are input edges r0 + 1, r0 + 2 and r0
     int n4, n5, n6;
-    uint8_t c4 = hinge(v[1], v[2], &n4);
-    uint8_t c5 = hinge(v[2], v[0], &n5);
-    uint8_t c6 = hinge(v[0], v[1], &n6);
+    uint8_t c4 = hinge(t, (r0 + 1) % 3, &n4);
+    uint8_t c5 = hinge(t, (r0 + 2) % 3, &n5);
+    uint8_t c6 = hinge(t, r0, &n6);
     const int idx[6] = {v[0], v[1], v[2], n4, n5, n6};
     for (int j = 0; j < 6; ++j) T.t_idx[(size_t)j * nt + t] = idx[j];
     T.t_bc[(size_t)0 * nt + t] = c4;
@@ -118,20 +142,21 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
   // ---- edge stencils (edge-hinge models only): interior edges, then clamped boundary edges
   std::vector<int32_t> ei[4];
   if (edge_model) {
-    for (const DirEdge &d : de) {
+    for (size_t i = 0; i < de.size(); ++i) {
+      const DirEdge &d = de[i];
       int p = (int)(d.key / N), q = (int)(d.key % N);
       if (p >= q) continue;
-      const DirEdge *tw = find((uint64_t)q * N + p);
-      if (!tw) continue;
+      if (twin[i] < 0) continue;
       ei[0].push_back(d.opp);
       ei[1].push_back(p);
       ei[2].push_back(q);
-      ei[3].push_back(tw->opp);
+      ei[3].push_back(de[twin[i]].opp);
     }
     T.ne_int = (int)ei[0].size();
-    for (const DirEdge &d : de) {
+    for (size_t i = 0; i < de.size(); ++i) {
+      const DirEdge &d = de[i];
       int p = (int)(d.key / N), q = (int)(d.key % N);
-      if (find((uint64_t)q * N + p)) continue;
+      if (twin[i] >= 0) continue;
       if (!is_clamped(p, q)) continue;
       ei[0].push_back(d.opp);
       ei[1].push_back(p);

@@ -62,3 +62,10 @@ def test_scaled_traffic_uses_the_capture_ratio_on_the_current_source():
     assert bench.measured_traffic("batch256", record=rec) == (None, None)
     stale = dict(rec, source_sha1="0" * 40)
     assert bench.scaled_traffic(8.0e9, record=stale) == (None, None, None)
+
+
+def test_bytes_without_vcycle_drop_only_the_cycle_terms():
+    info = {"n_verts": 1000, "nnz": 19000, "n_slots": 6000, "vcycle_bytes": 5e5}
+    stats = {"total_refine_rounds": 3, "total_pcg_iterations": 20}
+    full = bench.algorithmic_bytes(info, stats, 2)
+    assert full - bench.algorithmic_bytes_without_vcycle(info, stats, 2) == (3 + 20) * 5e5
