@@ -11,13 +11,11 @@
 namespace shl {
 namespace {
 
-// chord_k > 0: a later chord iteration of the exact backward-Euler step; only instances whose step is in a
-// chord iteration take part, with forces at their iterate positions xk. The FP32 kernel is held to 64
-// registers (8 blocks per SM): 32 instead of 24 resident warps hide more of each thread's dependent chain
-// (0.245 -> 0.220 ms per batch256 step, 40 bytes of spills); the FP64 one would spill heavily and keeps
-// its own.
+// FP64 forces of the instances in the tiles (FP64 steps, energies, shell_forces; FP32 instances evaluate their
+// forces inside the step kernel). chord_k > 0: a later iteration of the exact backward-Euler step; only
+// instances whose step is in such an iteration take part, with forces at their iterate positions xk.
 template <typename R>
-__global__ void __launch_bounds__(kForceBlock, sizeof(R) == 4 ? 8 : 1)
+__global__ void __launch_bounds__(kForceBlock, 1)
     k_forces(const Inst *__restrict__ insts, const Tile *__restrict__ tiles, int want_energy, int chord_k) {
   const Tile tl = tiles[blockIdx.x];
   const Inst &I = insts[tl.inst];
@@ -157,13 +155,12 @@ cudaError_t launch_gather_status(const Inst *d_insts, int n, InstStatus *d_out, 
   return cudaGetLastError();
 }
 
+// fp32 != 0 is not a launch of this kernel any more: FP32 forces are a phase of the step kernel
 cudaError_t launch_forces(const Inst *d_insts, const Tile *d_tiles, int n_tiles, int want_energy, int fp32,
                           cudaStream_t st, int chord_k) {
+  if (fp32) return cudaErrorInvalidValue;
   if (n_tiles <= 0) return cudaSuccess;
-  if (fp32)
-    k_forces<float><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy, chord_k);
-  else
-    k_forces<double><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy, chord_k);
+  k_forces<double><<<n_tiles, kForceBlock, 0, st>>>(d_insts, d_tiles, want_energy, chord_k);
   return cudaGetLastError();
 }
 
