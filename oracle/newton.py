@@ -27,7 +27,7 @@ also inside Newton, so their Newton iteration converges to the exact solution at
   J(v) = M + dt^2 K_T(x + dt v), R(v) the backward-Euler residual; stops at ||R(v_k)|| <= rtol ||R(0)||.
 * :func:`solve_static` -- Eq. 64: x_{k+1} = x_k + alpha dx, K_T(x_k) dx = f(x_k) + f_ext,
   alpha = min(1, eps_u / |dx|_inf); stops once |f(x_k) + f_ext| < eps_f (2-norm over free degrees of
-  freedom). Pinned vertices stay put.
+  freedom). Fixed components (every component of a pinned vertex) stay put.
 """
 from __future__ import annotations
 
@@ -153,8 +153,8 @@ def tangent_matrix(m: Model, x, frozen=False) -> sp.csr_matrix:
 
 
 def _pin_rows(m: Model, K):
-    """Identity rows and columns at pinned vertices."""
-    free = np.repeat(~m.pinned, 3).astype(np.float64)
+    """Identity rows and columns at the fixed components (every component of a pinned vertex)."""
+    free = (~m.fixed).ravel().astype(np.float64)
     D = sp.diags(free)
     return (D @ K @ D + sp.diags(1.0 - free)).tocsc()
 
@@ -184,9 +184,9 @@ def step_newton(m: Model, x, v, n_steps=1, max_iters=30, rtol=1e-10):
 
 
 def static_residual(m: Model, x):
-    """f(x) + f_ext at free vertices (zero at pinned ones): the residual of Eq. 64."""
+    """f(x) + f_ext at free components (zero at fixed ones): the residual of Eq. 64."""
     r = forces(m, x) + m.f_ext
-    r[m.pinned] = 0.0
+    r[m.fixed] = 0.0
     return r
 
 
@@ -205,7 +205,7 @@ def solve_static(m: Model, x0, eps_f=1e-3, eps_u=0.1, max_iters=1000, shift=Fals
         if shift:
             K = K + Ms
         dx = spla.spsolve(_pin_rows(m, K), r.ravel()).reshape(-1, 3)
-        dx[m.pinned] = 0.0
+        dx[m.fixed] = 0.0
         big = np.abs(dx).max()
         alpha = min(1.0, eps_u / big) if big > 0 else 1.0
         x = x + alpha * dx

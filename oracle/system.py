@@ -13,6 +13,11 @@ triangles of density * thickness * area / 3 (the paper does not give M). For pla
 this is exactly backward Euler, since the plate force is linear. Pinned vertices get an identity row
 and column and a zero right-hand side, so their velocity is zero.
 
+Per-component constraints (the symmetry conditions of Section 6.1's hemisphere: one or two displacement
+components of a vertex fixed, the others free) do not fit the scalar matrix: with them the step is solved on
+the 3V unknowns (vertex-major x, y, z), the matrix A (x) I_3 keeping the rows and columns of the free
+components and getting identity rows and columns, with zero right-hand sides, at the fixed ones.
+
 The linear system is solved directly (scipy SuperLU factorisation, computed once), so the oracle gives
 the exact solution of each step's system up to rounding.
 """
@@ -50,8 +55,15 @@ class Model:
     Dm_inv: np.ndarray          # [T,2,2]
     tri_area: np.ndarray        # [T]
     membrane: bool
+    fixed: Optional[np.ndarray] = None    # [V,3] bool: fixed components (all three at pinned vertices)
     A: Optional[sp.csc_matrix] = None
     _lu: object = None
+    _lu3: object = None
+
+    @property
+    def partial(self) -> bool:
+        """True when some vertex has fixed and free components (the step needs the 3V matrix)."""
+        return bool(np.any(self.fixed.any(axis=1) & ~self.fixed.all(axis=1)))
 
     @property
     def n_verts(self):
@@ -109,8 +121,10 @@ def _triangle_stencils(rest, topo, model, D_b):
 
 
 def build_model(tris, rest, model, E, nu, thickness, density, dt, pinned=None, clamped_edges=(),
-                gravity=(0.0, 0.0, 0.0), load_vtx=(), load_f=(), membrane=True, factor=True) -> Model:
-    """Rest-state precompute and constant matrix for one mesh (the 'create' step)."""
+                gravity=(0.0, 0.0, 0.0), load_vtx=(), load_f=(), membrane=True, factor=True,
+                fixed_dofs=None) -> Model:
+    """Rest-state precompute and constant matrix for one mesh (the 'create' step). ``fixed_dofs``: per-vertex
+    bit mask of fixed components (bit 0 x, bit 1 y, bit 2 z) or None; all three bits pin the vertex."""
     if model not in MODELS:
         raise ValueError(model)
     tris = np.asarray(tris, np.int64)
@@ -129,21 +143,31 @@ def build_model(tris, rest, model, E, nu, thickness, density, dt, pinned=None, c
     pin = np.zeros(V, bool) if pinned is None else np.asarray(pinned).astype(bool)
     if len(np.asarray(clamped_edges).ravel()):
         pin[np.asarray(clamped_edges).ravel()] = True
+    fixed = np.repeat(pin[:, None], 3, axis=1)
+    if fixed_dofs is not None:
+        bits = np.asarray(fixed_dofs).astype(np.int64)
+        fixed |= ((bits[:, None] >> np.arange(3)[None, :]) & 1).astype(bool)
+        pin |= fixed.all(axis=1)
     f_ext = mass[:, None] * np.asarray(gravity, np.float64)[None, :]
     lv = np.asarray(load_vtx, np.int64).ravel()
     if len(lv):
         np.add.at(f_ext, lv, np.asarray(load_f, np.float64).reshape(-1, 3))
-    m = Model(model, tris, rest, E, nu, thickness, density, dt, pin, f_ext, mass, sets, Dm_inv, area, membrane)
+    m = Model(model, tris, rest, E, nu, thickness, density, dt, pin, f_ext, mass, sets, Dm_inv, area, membrane,
+              fixed)
     if factor:
         m.A = system_matrix(m)
-        m._lu = spla.splu(m.A)
+        if m.partial:
+            m._lu3 = spla.splu(system_matrix3(m))
+        else:
+            m._lu = spla.splu(m.A)
     return m
 
 
 def from_scenario(sc, membrane=True, factor=True) -> Model:
     """Build the oracle model of a :class:`shellgen.Scenario`."""
     return build_model(sc.tris, sc.rest, sc.model, sc.E, sc.nu, sc.thickness, sc.density, sc.dt, sc.pinned,
-                       sc.clamped_edges, sc.gravity, sc.load_vtx, sc.load_f, membrane=membrane, factor=factor)
+                       sc.clamped_edges, sc.gravity, sc.load_vtx, sc.load_f, membrane=membrane, factor=factor,
+                       fixed_dofs=getattr(sc, "fixed_dofs", None))
 
 
 # ------------------------------------------------------------------ matrices
@@ -177,6 +201,28 @@ def system_matrix(m: Model) -> sp.csc_matrix:
     keep = sp.diags((~m.pinned).astype(np.float64))
     A = keep @ A @ keep + sp.diags(m.pinned.astype(np.float64))
     return A.tocsc()
+
+
+def system_matrix3(m: Model) -> sp.csc_matrix:
+    """The step matrix on the 3V unknowns (vertex-major x, y, z): (M + dt^2 (K_b + K_m)) (x) I_3 with identity
+    rows and columns at every fixed component."""
+    Kb, Km = stiffness_matrices(m)
+    A3 = sp.kron(sp.diags(m.mass) + (m.dt ** 2) * (Kb + Km), sp.identity(3), format="csr")
+    free = (~m.fixed).ravel().astype(np.float64)
+    return (sp.diags(free) @ A3 @ sp.diags(free) + sp.diags(1.0 - free)).tocsc()
+
+
+def solve_step_matrix(m: Model, b):
+    """A^-1 b for b [V,3] (direct SuperLU solve, factorised once): the scalar matrix on the three components
+    alike, or the 3V matrix when some vertex has fixed and free components."""
+    if m.partial:
+        if m._lu3 is None:
+            m._lu3 = spla.splu(system_matrix3(m))
+        return m._lu3.solve(np.ascontiguousarray(b).ravel()).reshape(-1, 3)
+    if m._lu is None:
+        m.A = system_matrix(m)
+        m._lu = spla.splu(m.A)
+    return m._lu.solve(b)
 
 
 # ------------------------------------------------------------------ forces / energy / step
@@ -213,9 +259,9 @@ def energy(m: Model, x, v):
 
 
 def rhs(m: Model, x, v):
-    """b = M v + dt (f(x) + f_ext), zero at pinned vertices."""
+    """b = M v + dt (f(x) + f_ext), zero at fixed components."""
     b = m.mass[:, None] * v + m.dt * (forces(m, x) + m.f_ext)
-    b[m.pinned] = 0.0
+    b[m.fixed] = 0.0
     return b
 
 
@@ -223,11 +269,8 @@ def step(m: Model, x, v, n_steps=1):
     """n_steps linearised backward-Euler steps; returns (x, v)."""
     x = np.array(x, np.float64, copy=True)
     v = np.array(v, np.float64, copy=True)
-    if m._lu is None:
-        m.A = system_matrix(m)
-        m._lu = spla.splu(m.A)
     for _ in range(n_steps):
-        v = m._lu.solve(rhs(m, x, v))
+        v = solve_step_matrix(m, rhs(m, x, v))
         x = x + m.dt * v
     return x, v
 
@@ -235,10 +278,10 @@ def step(m: Model, x, v, n_steps=1):
 # ------------------------------------------------------------------ exact backward Euler (chord iteration)
 def residual_nonlinear(m: Model, x, v, vn):
     """Backward-Euler residual of a candidate new velocity vn (Section 5, Eq. 62-63 without the
-    linearisation): R = M (vn - v) - dt (f(x + dt vn) + f_ext) at free vertices, R = vn at pinned ones.
+    linearisation): R = M (vn - v) - dt (f(x + dt vn) + f_ext) at free components, R = vn at fixed ones.
     R = 0 is the stationarity condition of the incremental potential in the velocity unknown."""
     R = m.mass[:, None] * (vn - v) - m.dt * (forces(m, x + m.dt * vn) + m.f_ext)
-    R[m.pinned] = vn[m.pinned]
+    R[m.fixed] = vn[m.fixed]
     return R
 
 
@@ -249,9 +292,6 @@ def step_nonlinear(m: Model, x, v, n_steps=1, max_iters=50, rtol=1e-8):
     Returns (x, v, iterations of each step)."""
     x = np.array(x, np.float64, copy=True)
     v = np.array(v, np.float64, copy=True)
-    if m._lu is None:
-        m.A = system_matrix(m)
-        m._lu = spla.splu(m.A)
     iters = []
     for _ in range(n_steps):
         vk = np.zeros_like(v)
@@ -259,7 +299,7 @@ def step_nonlinear(m: Model, x, v, n_steps=1, max_iters=50, rtol=1e-8):
         n0 = np.linalg.norm(R)
         k = 0
         while k < max_iters:
-            vk = vk - m._lu.solve(R)
+            vk = vk - solve_step_matrix(m, R)
             k += 1
             R = residual_nonlinear(m, x, v, vk)
             if np.linalg.norm(R) <= rtol * n0:
@@ -271,9 +311,9 @@ def step_nonlinear(m: Model, x, v, n_steps=1, max_iters=50, rtol=1e-8):
 
 
 def incremental_potential(m: Model, x, v, vn):
-    """Incremental potential of the step in the velocity unknown (pinned velocities are zero):
+    """Incremental potential of the step in the velocity unknown (fixed components of it are zero):
     E(vn) = 1/2 (vn - v)^T M (vn - v) + Psi(x + dt vn) - f_ext . (x + dt vn); its gradient in vn is
-    M (vn - v) - dt (f(x + dt vn) + f_ext) = R(vn) at free vertices, so backward Euler is its minimiser."""
+    M (vn - v) - dt (f(x + dt vn) + f_ext) = R(vn) at free components, so backward Euler is its minimiser."""
     d = vn - v
     xn = x + m.dt * vn
     return (0.5 * float(np.sum(m.mass[:, None] * d * d)) + membrane_energy(m, xn) + bending_energy(m, xn)

@@ -161,6 +161,9 @@ class Scenario:
     dt: float
     steps: int
     seed: Optional[int] = None
+    # per-vertex bit mask of fixed displacement components (bit 0 x, bit 1 y, bit 2 z), uint8 [V], or None;
+    # a vertex with all three bits set is pinned
+    fixed_dofs: Optional[np.ndarray] = None
 
     @property
     def n_verts(self) -> int:
@@ -364,3 +367,57 @@ def cantilever_tip(sc: Scenario) -> int:
     """Index of the mid node of the cantilever's loaded edge (where w_tip is read)."""
     right = np.asarray(sc.load_vtx)
     return int(right[np.argsort(sc.rest[right, 1])[len(right) // 2]])
+
+
+def hemisphere(model: str = "SS", n_around: int = 64, n_rings: int = 17, radius: float = 10.0,
+               cut_deg: float = 18.0, E: float = 6.825e7, nu: float = 0.3, thickness: float = 0.04,
+               load: float = 200.0, density: float = 1.0, dt: float = 1.0) -> Scenario:
+    """Hemispherical shell under alternating radial point loads (Section 6.1, geometrically non-linear
+    benchmark), the whole shell: radius ``radius``, a circular hole of half-angle ``cut_deg`` at the pole,
+    ``n_rings`` rings of ``n_around`` nodes from the equator (latitude 0) to the hole's edge (latitude
+    90 - cut_deg), 64 x 17 = 1088 nodes by default. Ring k, node j sits at latitude k (90 - cut_deg) /
+    (n_rings - 1) and longitude 2 pi j / n_around. Each quadrilateral cell is split into two triangles along
+    the diagonal that makes the mesh symmetric under the reflections x -> -x and y -> -y (from (j, k) to
+    (j + 1, k + 1) where j lies in the first or third quadrant of longitudes, the other diagonal in the
+    second and fourth), so the loaded problem has both symmetries. Triangles are counter-clockwise seen from
+    outside. Loads on the equator: ``load`` towards the centre at (+-radius, 0, 0) and away from it at
+    (0, +-radius, 0). Constraints (``fixed_dofs``): x fixed on the nodes of the y-z plane, y fixed on the
+    nodes of the x-z plane, and z also fixed on the hole's edge in the y-z plane. No gravity, no clamped
+    edges. ``n_around`` must be a multiple of 4. ``density`` and ``dt`` only enter a quasi-static solve
+    through the mass shift M / dt^2 of its linear systems."""
+    if n_around % 4 or n_around < 8 or n_rings < 2:
+        raise ValueError("n_around must be a multiple of 4 (>= 8) and n_rings >= 2")
+    lat = np.radians(90.0 - cut_deg) * np.arange(n_rings) / (n_rings - 1)
+    lon = 2.0 * np.pi * np.arange(n_around) / n_around
+    k, j = np.meshgrid(np.arange(n_rings), np.arange(n_around), indexing="ij")
+    k, j = k.ravel(), j.ravel()
+    rest = np.stack([radius * np.cos(lat[k]) * np.cos(lon[j]), radius * np.cos(lat[k]) * np.sin(lon[j]),
+                     radius * np.sin(lat[k])], axis=1)
+    q = n_around // 4
+    for jj, c in ((0, 0), (q, 1), (2 * q, 0), (3 * q, 1)):   # exact zeros on the symmetry planes
+        rest[j == jj, 1 - c] = 0.0
+    vid = lambda kk, jj: kk * n_around + (jj % n_around)
+    tris = []
+    for kk in range(n_rings - 1):
+        for jj in range(n_around):
+            a, b, c, d = vid(kk, jj), vid(kk, jj + 1), vid(kk + 1, jj + 1), vid(kk + 1, jj)
+            if (jj // q) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    tris = np.asarray(tris, np.int32)
+    fixed = np.zeros(rest.shape[0], np.uint8)
+    fixed[(j == q) | (j == 3 * q)] |= 1
+    fixed[(j == 0) | (j == 2 * q)] |= 2
+    fixed[((j == q) | (j == 3 * q)) & (k == n_rings - 1)] |= 4
+    lv = np.array([vid(0, 0), vid(0, 2 * q), vid(0, q), vid(0, 3 * q)], np.int32)
+    lf = load * np.array([[-1.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, -1.0, 0.0]])
+    return Scenario(f"hemisphere_{model}", tris, rest, rest.copy(), np.zeros_like(rest), model, E, nu, thickness,
+                    density, np.zeros(rest.shape[0], np.uint8), np.zeros((0, 2), np.int32), (0.0, 0.0, 0.0), lv,
+                    lf, dt, 1, fixed_dofs=fixed)
+
+
+def hemisphere_probes(sc: Scenario):
+    """Indices of the equator nodes at (radius, 0, 0) (loaded towards the centre: u_min is read there) and
+    at (0, radius, 0) (loaded outwards: v_max)."""
+    return int(sc.load_vtx[0]), int(sc.load_vtx[2])
