@@ -346,10 +346,15 @@ PAPER_CANTILEVER = {"EP": (5.388, 61), "ES": (5.387, 61), "FP": (6.056, 68), "FS
                     "SS": (6.072, 67)}
 
 
+# Section 6.1 Table, hemisphere (1088 nodes): u_min, v_max, Newton iterations (the shell models only)
+PAPER_HEMISPHERE = {"ES": (-4.072, 2.799, 56), "FS": (-5.752, 3.403, 84), "SS": (-5.923, 3.534, 87)}
+
+
 def static_record(gb):
-    """Quasi-static cantilever of Section 6.1 (17 x 3 nodes, end shear 4, eps_f = 1e-3, eps_u = 0.1) for the six
-    models on the GPU (FP64, Newton with the displacement limit, multigrid preconditioner): Newton steps, w_tip
-    and wall time per solve."""
+    """Quasi-static benchmarks of Section 6.1 on the GPU (FP64, Newton with the displacement limit eps_u = 0.1,
+    eps_f = 1e-3, multigrid preconditioner): the cantilever (17 x 3 nodes, end shear 4) for the six models
+    (w_tip) and the hemisphere (1088 nodes, radial loads 200, symmetry constraints) for the shell models (u_min,
+    v_max); Newton steps and wall time per solve, beside the Table's values."""
     import shellgen as sg
     out = {}
     for model in sg.MODELS:
@@ -365,6 +370,20 @@ def static_record(gb):
         out[model] = {"w_tip": float(x[tip, 2] - sc.rest[tip, 2]), "newton_steps": st["nl_iterations"],
                       "residual": st["rel_residual"], "wall_s": round(wall, 4),
                       "paper_w_tip": PAPER_CANTILEVER[model][0], "paper_iterations": PAPER_CANTILEVER[model][1]}
+        gb.shell_destroy(h)
+    for model in sg.SHELL_MODELS:
+        sc = sg.hemisphere(model)
+        h = gb.create_from_scenario(sc, precision="fp64", preconditioner="amg")
+        t0 = time.perf_counter()
+        st = gb.shell_solve_static(h, eps_f=1e-3, eps_u=0.1, max_iters=600)
+        wall = time.perf_counter() - t0
+        x, _ = gb.shell_get_state(h)
+        ia, ib = sg.hemisphere_probes(sc)
+        pu, pv, pit = PAPER_HEMISPHERE[model]
+        out["hemisphere_" + model] = {
+            "u_min": float(x[ia, 0] - sc.rest[ia, 0]), "v_max": float(x[ib, 1] - sc.rest[ib, 1]),
+            "newton_steps": st["nl_iterations"], "residual": st["rel_residual"], "wall_s": round(wall, 4),
+            "paper_u_min": pu, "paper_v_max": pv, "paper_iterations": pit}
         gb.shell_destroy(h)
     return out
 

@@ -96,7 +96,14 @@ typedef struct shell_material {
  * Boundary edges not listed as clamped are free (no edge stencil; the virtual node of a triangle
  * stencil is folded with w_L' = w_M + w_N - w_L). A clamped edge folds w_L' = w_L, measures transverse
  * displacement along the fixed rest normal of its stencil, and pins both end vertices. Pinned vertices
- * keep their position (zero velocity). Simply supported = free edges + pinned vertices. */
+ * keep their position (zero velocity). Simply supported = free edges + pinned vertices.
+ * Per-component constraints (fixed_dofs; the symmetry conditions of the Section 6.1 hemisphere): a fixed
+ * component of a vertex keeps its position, the others move. All three bits set pins the vertex. The
+ * assembled matrix is scalar (one entry per vertex pair, the same for x, y and z), so a vertex with fixed
+ * and free components keeps its matrix row; the solves project instead (every product, right-hand side,
+ * residual and preconditioned vector is zeroed at the fixed components: conjugate gradients on the free
+ * components of the same system). An instance with such vertices runs in the step kernel's Newton-capable
+ * variant, which carries the projection; shell_apply_matrix applies the assembled matrix without it. */
 typedef struct shell_bc {
   const uint8_t *pinned;          /* [V] nonzero = fixed, or NULL */
   int32_t n_clamped;              /* number of clamped boundary edges */
@@ -105,6 +112,8 @@ typedef struct shell_bc {
   int32_t n_loads;                /* point loads */
   const int32_t *load_vtx;        /* [n_loads] */
   const double *load_f;           /* [n_loads][3] newtons */
+  const uint8_t *fixed_dofs;      /* [V] bit mask of fixed components (1 = x, 2 = y, 4 = z; 7 pins the
+                                   * vertex), or NULL; bits above 4 are invalid (SHELL_ERR_INVALID_ARG) */
 } shell_bc;
 
 /* Device memory hooks: if alloc is NULL the library uses cudaMallocAsync / cudaFreeAsync on the handle's

@@ -70,7 +70,7 @@ class shell_material(C.Structure):
 class shell_bc(C.Structure):
     _fields_ = [("pinned", C.c_void_p), ("n_clamped", C.c_int32), ("clamped_edges", C.c_void_p),
                 ("gravity", C.c_double * 3), ("n_loads", C.c_int32), ("load_vtx", C.c_void_p),
-                ("load_f", C.c_void_p)]
+                ("load_f", C.c_void_p), ("fixed_dofs", C.c_void_p)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -257,7 +257,7 @@ class Handle:
 
 
 def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None, init_vel=None, pinned=None,
-                 clamped_edges=None, gravity=(0.0, 0.0, 0.0), load_vtx=None, load_f=None, dt=1e-2,
+                 clamped_edges=None, gravity=(0.0, 0.0, 0.0), load_vtx=None, load_f=None, fixed_dofs=None, dt=1e-2,
                  precision="fp64", pcg_rtol=0.0, refine_rtol=0.0, pcg_max_it=20000, refine_max=20,
                  stream=None, use_torch_allocator=True, preconditioner="auto", no_staging=False) -> Handle:
     """shell_create: rest-state precompute and constant-matrix assembly on the GPU (see include/shell.h)."""
@@ -268,6 +268,7 @@ def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None,
     x0 = _arr(init_xyz, np.float64, (V, 3))
     v0 = _arr(init_vel, np.float64, (V, 3))
     pin = _arr(pinned, np.uint8, (V,))
+    fd = _arr(fixed_dofs, np.uint8, (V,))
     ce = _arr(clamped_edges, np.int32, (-1, 2)) if clamped_edges is not None else np.zeros((0, 2), np.int32)
     lv = _arr(load_vtx, np.int32, (-1,)) if load_vtx is not None else np.zeros((0,), np.int32)
     lf = _arr(load_f, np.float64, (-1, 3)) if load_f is not None else np.zeros((0, 3), np.float64)
@@ -281,6 +282,7 @@ def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None,
     bc.n_loads = lv.shape[0]
     bc.load_vtx = _ptr(lv) if lv.shape[0] else None
     bc.load_f = _ptr(lf) if lv.shape[0] else None
+    bc.fixed_dofs = _ptr(fd)
     opts = make_options(dt, precision, pcg_rtol, refine_rtol, pcg_max_it, refine_max, stream, use_torch_allocator,
                         preconditioner, no_staging)
     out = C.c_void_p()
@@ -291,10 +293,11 @@ def shell_create(tris, rest, model, E, nu, thickness, density, *, init_xyz=None,
 
 def create_from_scenario(sc, precision="fp64", **kw) -> Handle:
     """shell_create from any object with the fields of a generated scenario (tris, rest, x0, v0, model, E, nu,
-    thickness, density, pinned, clamped_edges, gravity, load_vtx, load_f, dt)."""
+    thickness, density, pinned, clamped_edges, gravity, load_vtx, load_f, dt; fixed_dofs if present)."""
     return shell_create(sc.tris, sc.rest, sc.model, sc.E, sc.nu, sc.thickness, sc.density, init_xyz=sc.x0,
                         init_vel=sc.v0, pinned=sc.pinned, clamped_edges=sc.clamped_edges, gravity=sc.gravity,
-                        load_vtx=sc.load_vtx, load_f=sc.load_f, dt=sc.dt, precision=precision, **kw)
+                        load_vtx=sc.load_vtx, load_f=sc.load_f, fixed_dofs=getattr(sc, "fixed_dofs", None),
+                        dt=sc.dt, precision=precision, **kw)
 
 
 def shell_step(h: Handle, n_steps: int = 1, check: bool = True) -> dict:

@@ -229,6 +229,9 @@ void destroy_graph(shell_batch *b) {
   b->graph_tried = false;
 }
 
+// The step kernel's variant with the Newton tangent also carries the projection of per-component constraints.
+static bool uses_nt_variant(const Inst &I) { return (I.nl_newton && I.nl_max > 1) || I.fix != nullptr; }
+
 // Build the force tile lists and the persistent-solve schedule for the resident instances.
 int rebuild_tables(shell_batch *b) {
   destroy_graph(b);
@@ -260,9 +263,10 @@ int rebuild_tables(shell_batch *b) {
   for (int k = 0; k < n; ++k) {
     const Inst &hk = b->slots[b->active[k]]->h;
     (hk.precision == SHELL_FP64 ? any64 : any32) = true;
-    anynt = anynt || (hk.nl_newton && hk.nl_max > 1);
+    anynt = anynt || uses_nt_variant(hk);
   }
-  // a batch with a Newton instance runs the variant that carries the Newton tangent
+  // a batch with a Newton instance, or one with per-component constraints, runs the variant that carries the
+  // Newton tangent and the projection
   b->prec = anynt ? 3 : (any64 && any32) ? 0 : (any64 ? 1 : 2);
   // default occupancy: the 3-CTA variant for FP32 (fewest spills), else the variant's maximum
   const int occ_def = b->prec == 2 ? blocks_per_sm_cached(2, 3) : max_occ(b->prec);
@@ -746,7 +750,13 @@ std::vector<double> to_soa(const double *aos, int nv) {
 // on the host (the matrix is constant, so this happens once) and upload its levels: the transfers with the
 // smoother folded in (Ps in SELL-32, Rs with 4 lanes per row), the coarse operators with 4 lanes per row,
 // the dense operator of the coarse end of the cycle, and (FP32 instances) the gather lists of every product.
-int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
+// Per-component constraints (fixb: fixed-component bits per vertex, empty if none has fixed and free ones): the
+// hierarchy is built from A with the diagonal of each such vertex doubled. A itself can be nearly singular then
+// (with nothing pinned, a rigid motion costs only its mass), and a cycle of A amplifies those motions, which the
+// projected system has removed; the doubled diagonal ties the constrained vertices down instead. Level 0 then
+// carries that matrix's values, and the instance's inverse diagonal (Jacobi, and the level-0 pre-smoothing
+// done in the residual and update phases) becomes its own, so the cycle stays symmetric.
+int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage, const std::vector<uint8_t> &fixb) {
   Inst &I = h->h;
   cudaStream_t st = h->mem.st;
   if (mode == SHELL_PRECOND_JACOBI) return SHELL_OK;
@@ -776,6 +786,14 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
     if (nv < 256 || q.empty()) return SHELL_OK;
     std::nth_element(q.begin(), q.begin() + q.size() / 2, q.end());
     if (q[q.size() / 2] <= 30.0) return SHELL_OK;
+  }
+  bool own0 = false;   // level 0 differs from the step matrix (doubled diagonals)
+  for (int r = 0; r < (int)fixb.size(); ++r) {
+    if (fixb[r] == 0 || fixb[r] == 7) continue;
+    for (int k = A.ptr[r]; k < A.ptr[r + 1]; ++k)
+      if (A.col[k] == r) A.val[k] *= 2.0;
+    val[T.diag_pos[r]] *= 2.0;
+    own0 = true;
   }
   HostAmg H;
   build_amg(A, &H);
@@ -836,9 +854,9 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
       } else {
         D.a_ptr = I.sl_ptr;
         D.a_col = I.sl_col;
-        D.a_val32 = I.val32;
-        D.a_val64 = I.val64;
-        D.rs32 = I.rs32;
+        D.a_val32 = own0 ? C.take<float>(nnz_pad) : I.val32;
+        D.a_val64 = own0 ? C.take<double>(nnz_pad) : I.val64;
+        D.rs32 = own0 ? C.take<float>(n) : I.rs32;
         D.dinv32 = I.dinv32;
         D.dinv64 = I.dinv64;
       }
@@ -895,6 +913,12 @@ int setup_amg(shell_handle *h, const HostTopo &T, int mode, bool stage) {
       CK(up(D.rs32, f32(H.levels[l].rowsum), 4 * (size_t)D.n));
       CK(up(D.dinv64, H.levels[l].dinv.data(), 8 * (size_t)D.n));
       CK(up(D.dinv32, f32(H.levels[l].dinv), 4 * (size_t)D.n));
+    } else if (own0) {
+      CK(up(D.a_val64, val.data(), 8 * nnz_pad));
+      CK(up(D.a_val32, f32(val), 4 * nnz_pad));
+      CK(up(D.rs32, f32(H.levels[0].rowsum), 4 * (size_t)D.n));
+      CK(up(D.dinv64, H.levels[0].dinv.data(), 8 * (size_t)D.n));
+      CK(up(D.dinv32, f32(H.levels[0].dinv), 4 * (size_t)D.n));
     }
     if (l < L - 1) {
       CK(up(D.p_ptr, Ps[l].sl_ptr.data(), 4 * Ps[l].sl_ptr.size()));
@@ -992,6 +1016,21 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   if (bc)
     for (int k = 0; k < bc->n_loads; ++k)
       if (bc->load_vtx[k] < 0 || bc->load_vtx[k] >= nv) return SHELL_ERR_INVALID_ARG;
+  // fixed components per vertex: pinned and clamped-edge vertices have all three; a vertex with fixed and free
+  // components makes the instance's solves projected
+  std::vector<uint8_t> fixb(nv, 0);
+  bool partial = false;
+  if (bc) {
+    for (int i = 0; i < nv; ++i) {
+      if (bc->fixed_dofs && (bc->fixed_dofs[i] & ~7u)) return SHELL_ERR_INVALID_ARG;
+      fixb[i] = (bc->pinned && bc->pinned[i]) ? 7 : (bc->fixed_dofs ? bc->fixed_dofs[i] : 0);
+    }
+    for (int k = 0; k < 2 * bc->n_clamped; ++k) {
+      if (bc->clamped_edges[k] < 0 || bc->clamped_edges[k] >= nv) return SHELL_ERR_INVALID_ARG;
+      fixb[bc->clamped_edges[k]] = 7;
+    }
+    for (int i = 0; i < nv; ++i) partial = partial || (fixb[i] != 0 && fixb[i] != 7);
+  }
   int rc = check_device();
   if (rc != SHELL_OK) return rc;
 
@@ -1063,6 +1102,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     I.fext = C.take<double>(3 * (size_t)nv);
     I.mass = C.take<double>(nv);
     I.pinned = C.take<uint8_t>(nv);
+    I.fix = partial ? C.take<uint8_t>(nv) : nullptr;
     I.t_idx = C.take<int32_t>(6 * (size_t)nt);
     I.t_bc = C.take<uint8_t>(3 * (size_t)nt);
     I.t_mode = C.take<uint8_t>(nt);
@@ -1177,10 +1217,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   std::vector<double> x0 = to_soa(mesh->init_xyz ? mesh->init_xyz : mesh->rest_xyz, nv);
   std::vector<double> v0 = mesh->init_vel ? to_soa(mesh->init_vel, nv) : std::vector<double>((size_t)3 * nv, 0.0);
   std::vector<uint8_t> pin(nv, 0);
-  if (bc && bc->pinned)
-    for (int i = 0; i < nv; ++i) pin[i] = bc->pinned[i] ? 1 : 0;
-  if (bc)
-    for (int k = 0; k < 2 * bc->n_clamped; ++k) pin[bc->clamped_edges[k]] = 1;
+  for (int i = 0; i < nv; ++i) pin[i] = fixb[i] == 7 ? 1 : 0;
   auto up = [&](void *dst, const void *src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
   };
@@ -1191,6 +1228,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
   CKF(up(I.vprev2, v0.data(), 8 * v0.size()));
   CKF(up(I.vprev3, v0.data(), 8 * v0.size()));
   CKF(up(I.pinned, pin.data(), nv));
+  if (partial) CKF(up(I.fix, fixb.data(), nv));
   CKF(up(I.t_idx, T.t_idx.data(), 4 * T.t_idx.size()));
   CKF(up(I.t_bc, T.t_bc.data(), T.t_bc.size()));
   CKF(up(I.e_idx, T.e_idx.data(), 4 * T.e_idx.size()));
@@ -1235,7 +1273,7 @@ int shell_create(const shell_mesh *mesh, const shell_material *mat, int32_t mode
     return (flags & 1) ? SHELL_ERR_DEGENERATE : SHELL_ERR_SINGULAR_OPERATOR;
   }
 #undef CKF
-  rc = setup_amg(h, T, opt.preconditioner, !opt.no_staging);
+  rc = setup_amg(h, T, opt.preconditioner, !opt.no_staging, partial ? fixb : std::vector<uint8_t>());
   if (rc != SHELL_OK) {
     if (h->amg_block) h->mem.put(h->amg_block, h->amg_bytes);
     h->mem.put(h->block, h->block_bytes);
@@ -1264,7 +1302,7 @@ int shell_step(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
 int shell_step_noalloc(shell_handle *h, int32_t n_steps, shell_step_stats *stats) {
   if (!h || n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (h->batch) return SHELL_ERR_BUSY;
-  const bool newton = h->h.nl_newton && h->h.nl_max > 1;
+  const bool newton = uses_nt_variant(h->h);
   const int prec = newton ? 3 : (h->h.precision == SHELL_FP64 ? 1 : 2);
   int team = std::max(1, std::min(num_sms() * blocks_per_sm_cached(prec, prec == 2 ? 3 : 2), h->h.n_chunks));
   if (team > static_max_ctas()) return SHELL_ERR_STATIC_LIMIT;

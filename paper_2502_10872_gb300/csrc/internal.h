@@ -109,6 +109,8 @@ struct Inst {
   double *vk;                    // [3][nv] the iterate v_k itself (quasi-static limiter)
   double *mass;                  // [nv]
   uint8_t *pinned;               // [nv]
+  uint8_t *fix;                  // [nv] fixed-component bits (1 x, 2 y, 4 z) when some vertex has fixed and free
+                                 // components (projected solves, Newton-capable variant only), else null
 
   // triangle data (membrane for every model; bending stencil for FVM / smoothed hinges)
   int32_t *t_idx;                // [6][nt] (relabelled; -1 = virtual neighbour)

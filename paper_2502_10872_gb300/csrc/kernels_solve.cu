@@ -575,7 +575,7 @@ __device__ void phase_forces(const Inst &I, const Team &tm) {
   }              \
   }
 
-// b = M v + dt (f + f_ext) (zero at pinned vertices); warm start sol = 4 (v + v_prev2) - 6 v_prev - v_prev3;
+// b = M v + dt (f + f_ext) (zero at pinned vertices and fixed components); warm start sol = 4 (v + v_prev2) - 6 v_prev - v_prev3;
 // g64 = sol; partial ||b||^2
 // Chord iteration k > 0 of the exact backward-Euler step (forces at x + dt v_k, v_k in sol and g64):
 // b = M v + dt (f + f_ext) + (A - M) v_k, warm start v_k kept, so that the first residual b - A v_k is
@@ -611,6 +611,8 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
             for (int c = 0; c < 3; ++c) f[c] += double(cv[j][c]);
       }
       const bool pin = I.pinned[row] != 0;
+      unsigned fx = 0u;   // fixed components of a vertex with fixed and free ones
+      if constexpr (NT) fx = I.fix ? (unsigned)I.fix[row] : 0u;
       const double m = I.mass[row];
       double av[3] = {0.0, 0.0, 0.0};
       if (chord) {
@@ -632,7 +634,8 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
         // quasi-static: b = dt (f + f_ext) + J v_k, so that b - J v_k = dt (f + f_ext), the residual of Eq. 64
         double b = (I.nl_static ? 0.0 : m * v) + I.dt * (f[c] + I.fext[c * nv + row]);
         if (chord) b += av[c] - (I.nl_static ? 0.0 : m * I.sol[c * nv + row]);
-        if (pin) b = 0.0;
+        const bool fixed = pin || ((fx >> c) & 1u);
+        if (fixed) b = 0.0;
         I.b[c * nv + row] = b;
         bb += b * b;
         // initial guess: cubic extrapolation of the last four velocities, 4 (v + v_prev2) - 6 v_prev - v_prev3
@@ -640,7 +643,7 @@ __device__ void phase_rhs(const Inst &I, const Team &tm) {
         // leaves them, as they only shape the initial guess); zero for the quasi-static solve
         if (!chord) {
           const int k = c * nv + row;
-          sv[c] = (pin || I.nl_static) ? 0.0 : 4.0 * (v + I.vprev2[k]) - 6.0 * I.vprev[k] - I.vprev3[k];
+          sv[c] = (fixed || I.nl_static) ? 0.0 : 4.0 * (v + I.vprev2[k]) - 6.0 * I.vprev[k] - I.vprev3[k];
           I.sol[c * nv + row] = sv[c];
         }
       }
@@ -691,7 +694,15 @@ __device__ void phase_resid(const Inst &I, const Team &tm) {
           az += cz;
         }
       }
-      const double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
+      double r0 = I.b[row] - ax, r1 = I.b[nv + row] - ay, r2 = I.b[2 * nv + row] - az;
+      if constexpr (NT) {
+        if (I.fix) {   // projected residual: zero at the fixed components
+          const unsigned fx = I.fix[row];
+          if (fx & 1u) r0 = 0.0;
+          if (fx & 2u) r1 = 0.0;
+          if (fx & 4u) r2 = 0.0;
+        }
+      }
       I.r64[row] = r0;
       I.r64[nv + row] = r1;
       I.r64[2 * nv + row] = r2;
@@ -758,6 +769,12 @@ __device__ void phase_spmv(const Inst &I, const Team &tm) {
           ax += cx;
           ay += cy;
           az += cz;
+        }
+        if (I.fix) {   // projected product P A u (u is zero at the fixed components)
+          const unsigned fx = I.fix[row];
+          if (fx & 1u) ax = R(0);
+          if (fx & 2u) ay = R(0);
+          if (fx & 4u) az = R(0);
         }
       }
       w[row] = ax;
@@ -1035,9 +1052,12 @@ __device__ __forceinline__ void restrict_blk(const AmgDev &A, const AmgDev &C, b
   }
 }
 
-// up step of a level: y = x + omega D^-1 r + Ps yc (256-row blocks, Ps in SELL-32)
-template <typename R, bool ST>
-__device__ void lv_up(const AmgDev &A, const AmgDev &C, typename Vec<R>::G *y, const Team &tm) {
+// up step of a level: y = x + omega D^-1 r + Ps yc (256-row blocks, Ps in SELL-32). MK (level 0 of an instance
+// with per-component constraints): y is zeroed at the components fix marks, so the preconditioned vector stays
+// on the free components.
+template <typename R, bool ST, bool MK = false>
+__device__ void lv_up(const AmgDev &A, const AmgDev &C, typename Vec<R>::G *y, const Team &tm,
+                      const uint8_t *fix = nullptr) {
   typedef typename Vec<R>::G G;
   const G *x = reinterpret_cast<const G *>(A.x);
   const G *rr = reinterpret_cast<const G *>(A.r);
@@ -1058,7 +1078,16 @@ __device__ void lv_up(const AmgDev &A, const AmgDev &C, typename Vec<R>::G *y, c
     const G xi = ldg4(x + row);
     const G ri = ldg4(rr + row);
     const R d = om * dinv[row];
-    y[row] = Vec<R>::mk(R(xi.x) + d * R(ri.x) + ax, R(xi.y) + d * R(ri.y) + ay, R(xi.z) + d * R(ri.z) + az);
+    R yx = R(xi.x) + d * R(ri.x) + ax, yy = R(xi.y) + d * R(ri.y) + ay, yz = R(xi.z) + d * R(ri.z) + az;
+    if constexpr (MK) {
+      if (fix) {
+        const unsigned fx = fix[row];
+        if (fx & 1u) yx = R(0);
+        if (fx & 2u) yy = R(0);
+        if (fx & 4u) yz = R(0);
+      }
+    }
+    y[row] = Vec<R>::mk(yx, yy, yz);
   }
 }
 
@@ -1277,17 +1306,18 @@ __device__ bool coarsest(const Inst &I, const Team &tm) {
 }
 
 // Up step of level l in one team phase (coarse correction and post-smoothing); the output of level 0 is u
-// (in g).
-template <typename R>
+// (in g), projected onto the free components when MK and the instance has per-component constraints.
+template <typename R, bool MK = false>
 __device__ bool up_step(const Inst &I, int l, const Team &tm) {
   typedef typename Vec<R>::G G;
   const AmgDev &A = I.amg[l];
   const AmgDev &C = I.amg[l + 1];
   G *y = (l == 0) ? Vec<R>::g(I) : reinterpret_cast<G *>(A.y);
+  const uint8_t *fix = (MK && l == 0) ? I.fix : nullptr;
   if (staged<R>(A.hp, tm.cap))
-    lv_up<R, (sizeof(R) == 4)>(A, C, y, tm);
+    lv_up<R, (sizeof(R) == 4), MK>(A, C, y, tm, fix);
   else
-    lv_up<R, false>(A, C, y, tm);
+    lv_up<R, false, MK>(A, C, y, tm, fix);
   return team_sync(tm);
 }
 
@@ -1355,14 +1385,14 @@ __device__ bool dense_level(const Inst &I, const Team &tm) {
 // u in g (AoS). Expects the level-0 pre-smoothing (done by the phase that wrote r) and a team barrier
 // before it. The pre-smoothing of each coarser level is fused into the restriction that produces its
 // right-hand side. Returns false on abort.
-template <typename R>
+template <typename R, bool MK = false>
 __device__ bool vcycle(const Inst &I, const Team &tm) {
   const int top = I.amg_dense_level > 0 ? I.amg_dense_level : I.amg_levels - 1;
   for (int l = 0; l < top; ++l)
     if (!down_step<R>(I, l, tm)) return false;
   if (!(I.amg_dense_level > 0 ? dense_level<R>(I, tm) : coarsest<R>(I, tm))) return false;
   for (int l = top - 1; l >= 0; --l)
-    if (!up_step<R>(I, l, tm)) return false;
+    if (!up_step<R, MK>(I, l, tm)) return false;
   return true;
 }
 
@@ -1372,7 +1402,7 @@ __device__ bool vcycle(const Inst &I, const Team &tm) {
 template <typename R, bool NT>
 __device__ int cg_loop(const Inst &I, Team &tm, double *x, double tol2, int max_it, double *rho_out) {
   if (!team_sync(tm)) return -2;
-  if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
+  if (I.amg_levels > 0 && !vcycle<R, NT>(I, tm)) return -2;
   phase_spmv<R, NT>(I, tm);
   if (!team_sync(tm)) return -2;
   double red[3];
@@ -1386,7 +1416,7 @@ __device__ int cg_loop(const Inst &I, Team &tm, double *x, double tol2, int max_
   for (int it = 1; it <= max_it; ++it) {
     phase_update<R>(I, tm, R(alpha), R(beta), first, x, alpha);
     if (!team_sync(tm)) return -2;
-    if (I.amg_levels > 0 && !vcycle<R>(I, tm)) return -2;
+    if (I.amg_levels > 0 && !vcycle<R, NT>(I, tm)) return -2;
     phase_spmv<R, NT>(I, tm);
     if (!team_sync(tm)) return -2;
     team_reduce(I, tm, red);

@@ -58,4 +58,34 @@ def test_binding_structs_match_header_layout():
     # shell_options: double, int32(+pad), double, double, int32, int32, 4 pointers
     assert C.sizeof(binding.shell_options) == 8 + 8 + 8 + 8 + 4 + 4 + 4 * 8 + 8
     assert C.sizeof(binding.shell_step_stats) == 4 * 4 + 8 + 8 + 8 + 8 + 8
-    assert C.sizeof(binding.shell_bc) == 8 + 8 + 8 + 24 + 8 + 8 + 8
+    assert C.sizeof(binding.shell_bc) == 8 + 8 + 8 + 24 + 8 + 8 + 8 + 8
+
+
+def test_binding_struct_offsets_match_the_c_compiler(tmp_path):
+    """Every field offset and struct size of the ctypes mirrors equals the C compiler's for include/shell.h."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from pathlib import Path
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"shell_mesh": binding.shell_mesh, "shell_material": binding.shell_material,
+               "shell_bc": binding.shell_bc, "shell_options": binding.shell_options,
+               "shell_step_stats": binding.shell_step_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "shell.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    inc = Path(__file__).resolve().parents[1] / "include"
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", str(inc), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
