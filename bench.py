@@ -566,14 +566,12 @@ def main():
         barrier()
         t0 = time.perf_counter()
         for _ in range(Ke):
-            gb.shell_batch_set_states(b32, pin_x, pin_v)
-            gb.shell_batch_step(b32, 1)
-            gb.shell_batch_get_states(b32, pin_x, pin_v)
+            gb.shell_batch_step_states(b32, 1, pin_x, pin_v, pin_x, pin_v)
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
         e2e = {"value": V_total * Ke * world / te, "unit": "vertex-steps/s", "steps": Ke,
                "h2d_bytes_per_step": 48 * rows, "d2h_bytes_per_step": 48 * rows,
-               "api": "shell_batch_set_states + shell_batch_step + shell_batch_get_states, pinned host buffers"}
+               "api": "shell_batch_step_states (states in, one step, states out; one wait), pinned host buffers"}
 
     gb.shell_batch_destroy(b32)
     del h32

@@ -331,6 +331,14 @@ int shell_batch_capacity(shell_batch *b);
 int shell_batch_get_states(shell_batch *b, double *x, double *v);
 int shell_batch_set_states(shell_batch *b, const double *x, const double *v);
 int shell_batch_state_layout(shell_batch *b, int32_t *slots, int64_t *row_offsets);
+/* shell_batch_set_states(x_in, v_in), shell_batch_step(n_steps) and shell_batch_get_states(x_out, v_out) in one
+ * call: the copies in, the steps and the copies out are queued on the batch's stream behind one another and
+ * the call waits once, at the end (the three calls wait after each). x_in, v_in: both NULL (keep the device
+ * states) or both host buffers of the packed layout above; x_out, v_out likewise (NULL: no copy out; they may
+ * be x_in, v_in). Results, stats and errors are those of the three calls; on an error the states copied out
+ * are the committed ones. */
+int shell_batch_step_states(shell_batch *b, int32_t n_steps, const double *x_in, const double *v_in, double *x_out,
+                            double *v_out, shell_step_stats *stats);
 /* Device time of the last shell_batch_step, per step, in milliseconds: out[k] for k < n (n <= steps). */
 int shell_batch_step_times(shell_batch *b, float *out_ms, int32_t n);
 /* Kernel timing of later shell_batch_step calls: with on != 0 every step is launched directly (not from

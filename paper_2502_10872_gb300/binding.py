@@ -41,6 +41,7 @@ EXPORTS = (
     "shell_destroy", "shell_topology_summary", "shell_batch_create", "shell_batch_admit", "shell_batch_retire", "shell_batch_step",
     "shell_batch_capacity", "shell_batch_step_times", "shell_batch_set_profiling", "shell_batch_kernel_times",
     "shell_batch_autotune", "shell_batch_set_launch", "shell_batch_get_states", "shell_batch_set_states",
+    "shell_batch_step_states",
     "shell_batch_state_layout", "shell_batch_set_wait_limit", "shell_set_newton", "shell_solve_static",
     "shell_batch_destroy",
 )
@@ -137,6 +138,7 @@ def load_library(path: str = LIB_PATH):
         "shell_batch_set_launch": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
         "shell_batch_get_states": (C.c_int, [P, P, P]),
         "shell_batch_set_states": (C.c_int, [P, P, P]),
+        "shell_batch_step_states": (C.c_int, [P, C.c_int32, P, P, P, P, C.POINTER(shell_step_stats)]),
         "shell_batch_state_layout": (C.c_int, [P, P, P]),
         "shell_batch_set_wait_limit": (C.c_int, [P, C.c_int64]),
         "shell_set_newton": (C.c_int, [P, C.c_int32]),
@@ -536,6 +538,24 @@ def shell_batch_set_states(b: Batch, x, v):
     xa = _arr(x, np.float64, (rows, 3))
     va = _arr(v, np.float64, (rows, 3))
     _check(load_library().shell_batch_set_states(b.ptr, xa.ctypes.data, va.ctypes.data), "shell_batch_set_states")
+
+
+def shell_batch_step_states(b: Batch, n_steps: int, x_in=None, v_in=None, x_out=None, v_out=None,
+                            check: bool = True):
+    """shell_batch_set_states + shell_batch_step + shell_batch_get_states in one call with one wait (packed
+    [rows][3] FP64 host buffers; None keeps the device states / copies nothing out)."""
+    lib = load_library()
+    _, offs = shell_batch_state_layout(b)
+    rows = int(offs[-1])
+    for a in (x_in, v_in, x_out, v_out):
+        assert a is None or (a.dtype == np.float64 and a.flags.c_contiguous and a.shape == (rows, 3))
+    ptr = lambda a: None if a is None else a.ctypes.data
+    cap = lib.shell_batch_capacity(b.ptr)
+    stats = (shell_step_stats * max(1, cap))()
+    rc = lib.shell_batch_step_states(b.ptr, int(n_steps), ptr(x_in), ptr(v_in), ptr(x_out), ptr(v_out), stats)
+    if check:
+        _check(rc, "shell_batch_step_states")
+    return rc, {k: stats[k].as_dict() for k in range(cap) if k in b.members}
 
 
 def shell_batch_destroy(b: Batch):

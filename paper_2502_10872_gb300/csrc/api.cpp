@@ -550,7 +550,35 @@ void try_capture(shell_batch *b) {
   cudaGraphDestroy(g);
 }
 
-int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
+// Packed state copies of the resident instances, enqueued on the batch's stream (no synchronisation): with xin,
+// host -> device and unpack; else pack and device -> host into x, v. The tables must be current.
+static int enqueue_states(shell_batch *b, double *x, double *v, const double *xin, const double *vin) {
+  const size_t need = 48 * (size_t)b->rows_total;
+  if (b->pack_bytes < need) {
+    if (b->d_pack) b->mem.put(b->d_pack, b->pack_bytes);
+    b->d_pack = (double *)b->mem.get(need);
+    b->pack_bytes = b->d_pack ? need : 0;
+    if (!b->d_pack) return SHELL_ERR_OOM;
+  }
+  cudaStream_t st = b->mem.st;
+  const size_t n3 = 3 * (size_t)b->rows_total;
+  double *dx = b->d_pack, *dv = b->d_pack + n3;
+  if (xin) {
+    CK(cudaMemcpyAsync(dx, xin, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dv, vin, 8 * n3, cudaMemcpyHostToDevice, st));
+    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 1, st));
+  } else {
+    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 0, st));
+    CK(cudaMemcpyAsync(x, dx, 8 * n3, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(v, dv, 8 * n3, cudaMemcpyDeviceToHost, st));
+  }
+  return SHELL_OK;
+}
+
+// Step the batch n_steps times. xin/vin (host [rows][3], both or neither): states copied in before the steps;
+// xout/vout: states copied out after them; all enqueued on the batch's stream ahead of one synchronisation.
+int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats, const double *xin = nullptr,
+               const double *vin = nullptr, double *xout = nullptr, double *vout = nullptr) {
   if (n_steps < 0) return SHELL_ERR_INVALID_ARG;
   if (b->dirty) {
     int rc = rebuild_tables(b);
@@ -558,6 +586,15 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   }
   const int n = b->n_active;
   if (n == 0 || n_steps == 0) {
+    if (n > 0 && xin) {
+      int rc = enqueue_states(b, nullptr, nullptr, xin, vin);
+      if (rc != SHELL_OK) return rc;
+    }
+    if (n > 0 && xout) {
+      int rc = enqueue_states(b, xout, vout, nullptr, nullptr);
+      if (rc != SHELL_OK) return rc;
+    }
+    if (n > 0 && (xin || xout)) CK(cudaStreamSynchronize(b->mem.st));
     if (stats)
       for (size_t k = 0; k < b->slots.size(); ++k) stats[k] = shell_step_stats{0, 0, 0, SHELL_OK, 0, 0.0, 0, 0.0, 0, 0};
     return SHELL_OK;
@@ -567,6 +604,10 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
   std::vector<InstStatus> before(n), after(n);
   for (int k = 0; k < n; ++k) before[k] = b->slots[b->active[k]]->last_status;
   if (!b->graph_tried) try_capture(b);
+  if (xin) {   // after the capture, which records only the step
+    int rc = enqueue_states(b, nullptr, nullptr, xin, vin);
+    if (rc != SHELL_OK) return rc;
+  }
   const int n_ev = std::min(n_steps, 4096) + 1;
   while ((int)b->events.size() < n_ev) {
     cudaEvent_t e;
@@ -601,6 +642,10 @@ int batch_step(shell_batch *b, int n_steps, shell_step_stats *stats) {
       if (rc != SHELL_OK) return rc;
     }
     if ((s + 1) % ev_stride == 0 && ev < n_ev) CK(cudaEventRecord(b->events[ev++], st));
+  }
+  if (xout) {
+    int rc = enqueue_states(b, xout, vout, nullptr, nullptr);
+    if (rc != SHELL_OK) return rc;
   }
   CK(launch_gather_status(b->d_insts, n, b->d_status_out, b->sched.abort_flag, b->d_abort_out, st));
   int32_t aborted = 0;
@@ -1610,6 +1655,12 @@ int shell_batch_retire(shell_batch *b, int32_t slot) {
   return SHELL_OK;
 }
 
+int shell_batch_step_states(shell_batch *b, int32_t n_steps, const double *x_in, const double *v_in, double *x_out,
+                            double *v_out, shell_step_stats *stats) {
+  if (!b || (!x_in) != (!v_in) || (!x_out) != (!v_out)) return SHELL_ERR_INVALID_ARG;
+  return batch_step(b, n_steps, stats, x_in, v_in, x_out, v_out);
+}
+
 int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats) {
   if (!b) return SHELL_ERR_INVALID_ARG;
   return batch_step(b, n_steps, stats);
@@ -1625,26 +1676,9 @@ static int batch_states(shell_batch *b, double *x, double *v, const double *xin,
     if (rc != SHELL_OK) return rc;
   }
   if (b->n_active == 0) return SHELL_OK;
-  const size_t need = 48 * (size_t)b->rows_total;
-  if (b->pack_bytes < need) {
-    if (b->d_pack) b->mem.put(b->d_pack, b->pack_bytes);
-    b->d_pack = (double *)b->mem.get(need);
-    b->pack_bytes = b->d_pack ? need : 0;
-    if (!b->d_pack) return SHELL_ERR_OOM;
-  }
-  cudaStream_t st = b->mem.st;
-  const size_t n3 = 3 * (size_t)b->rows_total;
-  double *dx = b->d_pack, *dv = b->d_pack + n3;
-  if (xin) {
-    CK(cudaMemcpyAsync(dx, xin, 8 * n3, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(dv, vin, 8 * n3, cudaMemcpyHostToDevice, st));
-    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 1, st));
-  } else {
-    CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, dx, dv, 0, st));
-    CK(cudaMemcpyAsync(x, dx, 8 * n3, cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(v, dv, 8 * n3, cudaMemcpyDeviceToHost, st));
-  }
-  CK(cudaStreamSynchronize(st));
+  int rc = enqueue_states(b, x, v, xin, vin);
+  if (rc != SHELL_OK) return rc;
+  CK(cudaStreamSynchronize(b->mem.st));
   return SHELL_OK;
 }
 

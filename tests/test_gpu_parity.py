@@ -309,6 +309,40 @@ def test_batch_packed_states_roundtrip():
     gb.shell_batch_destroy(b)
 
 
+def test_batch_step_states_equals_set_step_get():
+    """shell_batch_step_states (copies in, steps, copies out, one wait) gives the states and statistics of
+    shell_batch_set_states + shell_batch_step + shell_batch_get_states, bitwise; NULL buffers keep the device
+    states or copy nothing; zero steps only copy."""
+    scs = sg.mixed_batch(6, seed=35, side_lo=4, side_hi=40)
+    runs = []
+    for fused in (False, True):
+        b = gb.shell_batch_create(1 << 40)
+        hs = [gb.create_from_scenario(sc, precision="fp32_refine") for sc in scs]
+        for h in hs:
+            gb.shell_batch_admit(b, h)
+        gb.shell_batch_step(b, 2)
+        x, v = gb.shell_batch_get_states(b)
+        x, v = np.ascontiguousarray(x * 1.0001), np.ascontiguousarray(v * 0.5)
+        if fused:
+            xo, vo = np.empty_like(x), np.empty_like(v)
+            rc, st = gb.shell_batch_step_states(b, 3, x, v, xo, vo)
+            rc2, _ = gb.shell_batch_step_states(b, 2)                  # device states kept, nothing copied
+            x2, v2 = np.empty_like(x), np.empty_like(v)
+            gb.shell_batch_step_states(b, 0, None, None, x2, v2)        # zero steps: copy out only
+        else:
+            gb.shell_batch_set_states(b, x, v)
+            rc, st = gb.shell_batch_step(b, 3)
+            xo, vo = gb.shell_batch_get_states(b)
+            rc2, _ = gb.shell_batch_step(b, 2)
+            x2, v2 = gb.shell_batch_get_states(b)
+        assert rc == 0 and rc2 == 0
+        runs.append((xo, vo, x2, v2, {k: (s["steps_done"], s["total_pcg_iterations"]) for k, s in st.items()}))
+        gb.shell_batch_destroy(b)
+    for a, c in zip(runs[0][:4], runs[1][:4]):
+        assert np.array_equal(a, c)
+    assert runs[0][4] == runs[1][4]
+
+
 @pytest.mark.parametrize("case", ["cyl96_SS", "jitter160_SP", "batch6"])
 def test_shared_memory_staging_is_bitwise_neutral(case):
     """FP32 products that stage each 256-row block's gathered vector entries in shared memory read the same
