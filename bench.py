@@ -348,6 +348,8 @@ PAPER_CANTILEVER = {"EP": (5.388, 61), "ES": (5.387, 61), "FP": (6.056, 68), "FS
 
 # Section 6.1 Table, hemisphere (1088 nodes): u_min, v_max, Newton iterations (the shell models only)
 PAPER_HEMISPHERE = {"ES": (-4.072, 2.799, 56), "FS": (-5.752, 3.403, 84), "SS": (-5.923, 3.534, 87)}
+# Section 6.1 Table, linear plate bending: seconds for one linear solve on 7,459 nodes (32-core CPU)
+PAPER_LINEAR_PLATE_S = {"EP": 1.758, "ES": 1.778, "FP": 3.713, "FS": 3.788, "SP": 3.620, "SS": 3.759}
 
 
 def static_record(gb):
@@ -384,6 +386,21 @@ def static_record(gb):
             "u_min": float(x[ia, 0] - sc.rest[ia, 0]), "v_max": float(x[ib, 1] - sc.rest[ib, 1]),
             "newton_steps": st["nl_iterations"], "residual": st["rel_residual"], "wall_s": round(wall, 4),
             "paper_u_min": pu, "paper_v_max": pv, "paper_iterations": pit}
+        gb.shell_destroy(h)
+    # linear plate bending (simply supported square, 86 x 86 = 7,396 nodes, pressure scaled to the linear
+    # regime): centre deflection over Timoshenko's, and the wall time of the solve (forces, Newton steps)
+    for model in sg.MODELS:
+        sc = sg.linear_plate(model, 85, "regular")
+        h = gb.create_from_scenario(sc, precision="fp64", preconditioner="amg")
+        t0 = time.perf_counter()
+        st = gb.shell_solve_static(h, eps_f=1e-3, eps_u=0.1, max_iters=20)
+        wall = time.perf_counter() - t0
+        x, _ = gb.shell_get_state(h)
+        wref = 0.048744 * 9.81e-3 * 8.0 ** 4 * (1 - 0.3 ** 2) / (2e11 * 0.01 ** 3)
+        out["linear_plate_" + model] = {
+            "w_over_timoshenko": float((x[:, 2] - sc.rest[:, 2]).max() / wref), "newton_steps": st["nl_iterations"],
+            "pcg_iterations": st["total_pcg_iterations"], "wall_s": round(wall, 4),
+            "paper_wall_s": PAPER_LINEAR_PLATE_S[model], "mesh": "regular, 7,396 nodes"}
         gb.shell_destroy(h)
     return out
 
