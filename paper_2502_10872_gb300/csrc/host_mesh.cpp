@@ -43,16 +43,25 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     if (a == b || b == c || a == c) return SHELL_ERR_INVALID_ARG;
   }
 
-  // ---- directed edges
+  // ---- directed edges, sorted by key p * nv + q: bucketed by the source vertex p (a counting sort), then
+  // ordered by q inside each bucket (a few entries)
   std::vector<DirEdge> de((size_t)nt * 3);
-  for (int t = 0; t < nt; ++t) {
-    const int32_t *v = tris + 3 * t;
-    for (int k = 0; k < 3; ++k) {
-      int p = v[k], q = v[(k + 1) % 3], r = v[(k + 2) % 3];
-      de[3 * (size_t)t + k] = {(uint64_t)p * N + (uint64_t)q, t, r};
+  std::vector<int32_t> out_ptr(nv + 1, 0);   // de[out_ptr[p] .. out_ptr[p + 1]): the edges leaving p
+  for (size_t i = 0; i < (size_t)nt * 3; ++i) out_ptr[tris[i] + 1]++;
+  for (int i = 0; i < nv; ++i) out_ptr[i + 1] += out_ptr[i];
+  {
+    std::vector<int32_t> fill(out_ptr.begin(), out_ptr.end() - 1);
+    for (int t = 0; t < nt; ++t) {
+      const int32_t *v = tris + 3 * t;
+      for (int k = 0; k < 3; ++k) {
+        const int p = v[k], q = v[(k + 1) % 3], r = v[(k + 2) % 3];
+        de[fill[p]++] = {(uint64_t)p * N + (uint64_t)q, t, r};
+      }
     }
   }
-  std::sort(de.begin(), de.end(), [](const DirEdge &x, const DirEdge &y) { return x.key < y.key; });
+  for (int p = 0; p < nv; ++p)
+    for (int i = out_ptr[p] + 1; i < out_ptr[p + 1]; ++i)   // insertion sort: keys are distinct or an error
+      for (int j = i; j > out_ptr[p] && de[j].key < de[j - 1].key; --j) std::swap(de[j], de[j - 1]);
   for (size_t i = 1; i < de.size(); ++i) {
     if (de[i].key == de[i - 1].key) {
       // the same directed edge twice: either >2 triangles on the edge or a flipped neighbour
@@ -68,25 +77,21 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     auto it = std::lower_bound(de.begin(), de.end(), key, [](const DirEdge &x, uint64_t k) { return x.key < k; });
     return (it != de.end() && it->key == key) ? &*it : nullptr;
   };
-  // twin[i]: index in de of the reverse of directed edge i (-1 on the boundary), by one merge of de with its
-  // reversed keys in sorted order; at[3 t + k]: index in de of triangle t's edge k. Lookups of the hot loops
-  // below then cost O(1) instead of a binary search over all directed edges.
+  // twin[i]: index in de of the reverse of directed edge i (-1 on the boundary), found in the bucket of its
+  // target vertex; at[3 t + k]: index in de of triangle t's edge k. Lookups of the hot loops below then cost
+  // O(1) instead of a binary search over all directed edges.
   std::vector<int32_t> twin(de.size(), -1), at(de.size());
-  {
-    std::vector<std::pair<uint64_t, int32_t>> rev(de.size());
-    for (size_t i = 0; i < de.size(); ++i) {
-      const uint64_t p = de[i].key / N, q = de[i].key % N;
-      rev[i] = {q * N + p, (int32_t)i};
-      const int32_t *v = tris + 3 * (size_t)de[i].tri;
-      const int k = (v[0] == (int)p) ? 0 : (v[1] == (int)p) ? 1 : 2;
-      at[3 * (size_t)de[i].tri + k] = (int32_t)i;
-    }
-    std::sort(rev.begin(), rev.end());
-    size_t j = 0;
-    for (const auto &pr : rev) {
-      while (j < de.size() && de[j].key < pr.first) ++j;
-      if (j < de.size() && de[j].key == pr.first) twin[pr.second] = (int32_t)j;
-    }
+  for (size_t i = 0; i < de.size(); ++i) {
+    const uint64_t p = de[i].key / N, q = de[i].key % N;
+    const uint64_t rk = q * N + p;
+    for (int j = out_ptr[q]; j < out_ptr[q + 1]; ++j)
+      if (de[j].key == rk) {
+        twin[i] = j;
+        break;
+      }
+    const int32_t *v = tris + 3 * (size_t)de[i].tri;
+    const int k = (v[0] == (int)p) ? 0 : (v[1] == (int)p) ? 1 : 2;
+    at[3 * (size_t)de[i].tri + k] = (int32_t)i;
   }
 
   // ---- clamped boundary edges (undirected keys)
@@ -195,7 +200,8 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
     }
   }
 
-  // ---- sparsity: every pair of vertices that share a bending stencil or a membrane triangle
+  // ---- sparsity: every pair of vertices that share a bending stencil or a membrane triangle. A row's distinct
+  // columns are collected with a marker array (mark[c] == i: c is already in row i), then only they are sorted.
   auto stencil_of_slot = [&](int s, int *verts) -> int {   // returns vertex count, fills verts
     if (s < nt * T.kt) {
       int t = s / T.kt;
@@ -210,18 +216,21 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
   std::vector<int32_t> row_ptr(nv + 1, 0);
   std::vector<int32_t> cols;
   cols.reserve((size_t)nv * 20);
-  std::vector<int32_t> tmp;
+  std::vector<int32_t> tmp, mark(nv, -1);
   for (int i = 0; i < nv; ++i) {
     tmp.clear();
     tmp.push_back(i);
+    mark[i] = i;
     for (int q = T.vtx_ptr[i]; q < T.vtx_ptr[i + 1]; ++q) {
       int verts[6];
       int k = stencil_of_slot(T.vtx_slot[q], verts);
       for (int j = 0; j < k; ++j)
-        if (verts[j] >= 0) tmp.push_back(verts[j]);
+        if (verts[j] >= 0 && mark[verts[j]] != i) {
+          mark[verts[j]] = i;
+          tmp.push_back(verts[j]);
+        }
     }
     std::sort(tmp.begin(), tmp.end());
-    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
     cols.insert(cols.end(), tmp.begin(), tmp.end());
     row_ptr[i + 1] = (int32_t)cols.size();
   }
@@ -258,60 +267,50 @@ int build_topology(int nv, int nt, const int32_t *tris, int n_clamped, const int
       }
     }
   }
-  auto position = [&](int r, int c) -> int {
-    auto b = cols.begin() + row_ptr[r], e = cols.begin() + row_ptr[r + 1];
-    auto it = std::lower_bound(b, e, c);
-    int k = (int)(it - b);
-    int s = r / 32, l = r % 32;
-    return T.sl_ptr[s] + k * 32 + l;
-  };
-
   // ---- assembly sources. Local matrix layout:
   //   triangle-stencil models: [nt][36] bending (L^T W L), then [nt][9] membrane
   //   edge-hinge models:       [nt][9] membrane, then [ne][16] bending (w L L^T)
-  std::vector<std::pair<int32_t, int32_t>> src;   // (position, local index)
+  // Generated row by row from the row's slots, the SELL position of (r, c) from a column -> rank map of row r;
+  // a first pass counts the entries of every position, a second fills them in. Per position the sources come
+  // in increasing local index: the bending (triangle models) or membrane (edge models) entries of the row's
+  // slots in slot order first, then the other kind in slot order.
   const int mem_off = edge_model ? 0 : nt * 36;
   const int edge_off = nt * 9;
   T.n_local = edge_model ? nt * 9 + T.ne * 16 : nt * 45;
-  src.reserve((size_t)T.n_local);
-  if (!edge_model) {
-    for (int t = 0; t < nt; ++t)
-      for (int j = 0; j < 6; ++j) {
-        int r = T.t_idx[(size_t)j * nt + t];
-        if (r < 0) continue;
-        for (int k = 0; k < 6; ++k) {
-          int c = T.t_idx[(size_t)k * nt + t];
-          if (c < 0) continue;
-          src.push_back({position(r, c), t * 36 + j * 6 + k});
+  std::vector<int32_t> rank(nv, -1);
+  auto row_entries = [&](int r, auto &&emit) {
+    for (int k = row_ptr[r]; k < row_ptr[r + 1]; ++k) rank[cols[k]] = k - row_ptr[r];
+    const int base = T.sl_ptr[r / 32] + r % 32;
+    const int q0 = T.vtx_ptr[r], q1 = T.vtx_ptr[r + 1];
+    for (int pass = 0; pass < 2; ++pass)
+      for (int q = q0; q < q1; ++q) {
+        const int sl = T.vtx_slot[q];
+        if (sl < nt * T.kt) {
+          const int t = sl / T.kt, j = sl % T.kt;
+          if (!edge_model && pass == 0) {            // bending of the triangle stencil
+            for (int k = 0; k < 6; ++k) {
+              const int c = T.t_idx[(size_t)k * nt + t];
+              if (c >= 0) emit(base + 32 * rank[c], t * 36 + j * 6 + k);
+            }
+          } else if ((edge_model ? pass == 0 : pass == 1) && j < 3) {   // membrane of the triangle
+            for (int b = 0; b < 3; ++b) emit(base + 32 * rank[T.t_idx[(size_t)b * nt + t]], mem_off + t * 9 + j * 3 + b);
+          }
+        } else if (pass == 1) {                      // edge stencil (edge-hinge models)
+          const int e = (sl - nt * T.kt) / 4, j = (sl - nt * T.kt) % 4;
+          for (int k = 0; k < 4; ++k) {
+            const int c = T.e_idx[(size_t)k * T.ne + e];
+            if (c >= 0) emit(base + 32 * rank[c], edge_off + e * 16 + j * 4 + k);
+          }
         }
       }
-  }
-  for (int t = 0; t < nt; ++t)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        int r = T.t_idx[(size_t)a * nt + t], c = T.t_idx[(size_t)b * nt + t];
-        src.push_back({position(r, c), mem_off + t * 9 + a * 3 + b});
-      }
-  if (edge_model) {
-    for (int e = 0; e < T.ne; ++e)
-      for (int j = 0; j < 4; ++j) {
-        int r = T.e_idx[(size_t)j * T.ne + e];
-        if (r < 0) continue;
-        for (int k = 0; k < 4; ++k) {
-          int c = T.e_idx[(size_t)k * T.ne + e];
-          if (c < 0) continue;
-          src.push_back({position(r, c), edge_off + e * 16 + j * 4 + k});
-        }
-      }
-  }
+  };
   T.asm_ptr.assign(nnz_pad + 1, 0);
-  for (auto &pr : src) T.asm_ptr[pr.first + 1]++;
+  for (int r = 0; r < nv; ++r) row_entries(r, [&](int pos, int) { T.asm_ptr[pos + 1]++; });
   for (int p = 0; p < nnz_pad; ++p) T.asm_ptr[p + 1] += T.asm_ptr[p];
-  T.asm_src.resize(src.size());
+  T.asm_src.resize(T.asm_ptr[nnz_pad]);
   {
     std::vector<int32_t> fill(T.asm_ptr.begin(), T.asm_ptr.end() - 1);
-    // src is generated in increasing local index order, so each position's list is ordered
-    for (auto &pr : src) T.asm_src[fill[pr.first]++] = pr.second;
+    for (int r = 0; r < nv; ++r) row_entries(r, [&](int pos, int local) { T.asm_src[fill[pos]++] = local; });
   }
   return SHELL_OK;
 }
