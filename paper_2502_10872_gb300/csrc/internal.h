@@ -20,9 +20,9 @@ constexpr int kSlice = 32;          // SELL slice height (one warp)
 constexpr int kBlock = 256;         // threads of every CTA of the persistent solve kernel
 constexpr int kForceBlock = 128;    // threads of a force tile
 constexpr int kMaxTeamWaitMs = 4000;  // default bound of a team-barrier wait (Sched::wait_ns)
-constexpr int kBarWords = 64;       // barrier words per team: arrival count at [0], generation at [32]
-                                    // (separate 128-byte lines, so spinning readers do not contend with
-                                    // the arrival atomics)
+constexpr int kBarWords = 64;       // barrier words per team (256 bytes): a 64-bit arrival counter at [0, 2),
+                                    // the rest unused (one team's words do not share a cache line with
+                                    // another team's)
 
 // stencil modes
 enum : uint8_t { MODE_PLATE = 0, MODE_SHELL = 1, MODE_FIXED = 2, MODE_NONE = 3 };

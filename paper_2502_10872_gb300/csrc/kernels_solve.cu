@@ -83,22 +83,27 @@ __device__ inline double *part_of(const Inst &I, const Team &tm, int ch) {
   return I.part + 4 * ((size_t)tm.bank * I.n_chunks + ch);
 }
 
+__device__ inline unsigned long long ld_acquire64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Bounded global-memory barrier among `parties` arrivals on the team's words (thread 0 of the caller only).
+// The team's 64-bit arrival counter only grows: it is zeroed when the team layout is built (and after an
+// abandoned launch), and every CTA of a team passes the same barriers, so an episode starts at a multiple
+// of `parties` and ends when the counter reaches the next one. The last arrival's own increment releases the
+// others (no reset or generation word to write after it), and no word is read before arriving.
 // Returns 0 if it gave up (timeout, or abort raised elsewhere).
 __device__ int global_arrive_wait(const Team &tm, unsigned int parties) {
-  unsigned int *count = tm.bar;
-  unsigned int *gen = tm.bar + kBarWords / 2;
-  const unsigned int g = ld_acquire(gen);
-  __threadfence();
-  const unsigned int arrived = atomicAdd(count, 1u);
-  if (arrived == parties - 1u) {
-    atomicExch(count, 0u);
-    __threadfence();
-    atomicAdd(gen, 1u);
-  } else {
+  unsigned long long *count = reinterpret_cast<unsigned long long *>(tm.bar);
+  __threadfence();   // this CTA's writes of the phase are visible before its arrival
+  const unsigned long long o = atomicAdd(count, 1ull);
+  const unsigned long long target = (o / parties + 1ull) * parties;
+  if (o + 1ull != target) {
     const unsigned long long t0 = gtimer();
     const unsigned long long limit = tm.wait_ns;
-    while (ld_acquire(gen) == g) {
+    while (ld_acquire64(count) < target) {
       if (ld_volatile_i(tm.abort_flag)) return 0;
       if (gtimer() - t0 > limit) {
         atomicExch(tm.abort_flag, 1);
