@@ -324,8 +324,10 @@ int shell_batch_retire(shell_batch *b, int32_t slot);
  * first error met, or SHELL_OK. */
 int shell_batch_step(shell_batch *b, int32_t n_steps, shell_step_stats *stats);
 int shell_batch_capacity(shell_batch *b);
-/* Packed state transfer for every resident instance in one copy each way: x and v are host buffers of
- * [rows][3] FP64 (pinned memory recommended), the instances' rows concatenated in increasing slot order.
+/* Packed state transfer for every resident instance in one pass each way: x and v are host buffers of
+ * [rows][3] FP64, the instances' rows concatenated in increasing slot order. Page-locked buffers (cudaHostAlloc,
+ * cudaHostRegister) are read or written in place by the state kernel over the host link; pageable ones are
+ * copied through a device staging buffer (two copies each way, slower). The values are the same either way.
  * shell_batch_state_layout returns the number of resident instances and fills (either may be NULL)
  * slots[k] (the k-th resident slot) and row_offsets[k] (its first row; row_offsets[count] = rows). */
 int shell_batch_get_states(shell_batch *b, double *x, double *v);

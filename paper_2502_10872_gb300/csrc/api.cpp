@@ -550,19 +550,41 @@ void try_capture(shell_batch *b) {
   cudaGraphDestroy(g);
 }
 
+// Device address of a host buffer that the GPU can read and write in place: page-locked memory
+// (cudaHostAlloc, cudaHostRegister, torch's pinned tensors) is mapped into the device's address space under
+// unified addressing. Null for pageable memory, or memory not mapped for the current device.
+static double *mapped_host(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<double *>(a.devicePointer) : nullptr;
+}
+
 // Packed state copies of the resident instances, enqueued on the batch's stream (no synchronisation): with xin,
 // host -> device and unpack; else pack and device -> host into x, v. The tables must be current.
+// Page-locked host buffers are read (written) in place by the unpack (pack) kernel over the host link, with
+// no staging copy; pageable ones go through a device staging buffer and two copies each way.
 static int enqueue_states(shell_batch *b, double *x, double *v, const double *xin, const double *vin) {
-  const size_t need = 48 * (size_t)b->rows_total;
+  cudaStream_t st = b->mem.st;
+  {
+    double *mx = mapped_host(xin ? xin : x), *mv = mapped_host(xin ? vin : v);
+    if (mx && mv) {
+      CK(launch_pack_states(b->d_insts, b->n_active, b->d_offs, b->rows_total, mx, mv, xin ? 1 : 0, st));
+      return SHELL_OK;
+    }
+  }
+  const size_t n3 = 3 * (size_t)b->rows_total;
+  const size_t n3a = (n3 + 1) & ~size_t(1);   // v starts on a 16-byte boundary (vector state kernel)
+  const size_t need = 8 * (n3a + n3);
   if (b->pack_bytes < need) {
     if (b->d_pack) b->mem.put(b->d_pack, b->pack_bytes);
     b->d_pack = (double *)b->mem.get(need);
     b->pack_bytes = b->d_pack ? need : 0;
     if (!b->d_pack) return SHELL_ERR_OOM;
   }
-  cudaStream_t st = b->mem.st;
-  const size_t n3 = 3 * (size_t)b->rows_total;
-  double *dx = b->d_pack, *dv = b->d_pack + n3;
+  double *dx = b->d_pack, *dv = b->d_pack + n3a;
   if (xin) {
     CK(cudaMemcpyAsync(dx, xin, 8 * n3, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dv, vin, 8 * n3, cudaMemcpyHostToDevice, st));

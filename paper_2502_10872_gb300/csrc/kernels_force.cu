@@ -108,6 +108,7 @@ __device__ inline int find_inst(const long long *offs, int n, long long row) {
   }
   return lo;
 }
+// One row per thread (any alignment of the packed buffers).
 __global__ void k_pack_states(const Inst *__restrict__ insts, int n, const long long *__restrict__ offs, double *x,
                               double *v, int unpack) {
   const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,6 +123,73 @@ __global__ void k_pack_states(const Inst *__restrict__ insts, int n, const long 
     } else {
       x[3 * row + c] = I.x[c * I.nv + i];
       v[3 * row + c] = I.v[c * I.nv + i];
+    }
+  }
+}
+
+// Packed buffers with 16-byte aligned bases: each warp moves the 64 rows [64 w, 64 w + 64) as one contiguous
+// run of 1,536 bytes per array, lane L of pass j taking the 16-byte chunk 32 j + L (three fully coalesced
+// passes, also over the host link when the buffers are mapped host memory), and the rows are distributed
+// through shared memory to the per-instance SoA arrays (lane L: rows 64 w + L and 64 w + 32 + L). A run
+// ending on half a chunk moves its last value alone.
+constexpr int kPackRowsPerWarp = 64;
+__global__ void __launch_bounds__(256) k_pack_states_vec(const Inst *__restrict__ insts, int n,
+                                                         const long long *__restrict__ offs, double *x, double *v,
+                                                         int unpack) {
+  __shared__ double sx[8][3 * kPackRowsPerWarp], sv[8][3 * kPackRowsPerWarp];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long rows = offs[n];
+  const long long r0 = ((long long)blockIdx.x * 8 + w) * kPackRowsPerWarp;
+  if (r0 >= rows) return;
+  const long long d0 = 3 * r0;
+  const int nd = (int)(3 * (rows - r0 < kPackRowsPerWarp ? rows - r0 : kPackRowsPerWarp));   // doubles of the run
+  double *bx = sx[w], *bv = sv[w];
+  if (unpack) {
+    for (int j = 0; j < 3; ++j) {
+      const int q = 2 * (32 * j + lane);
+      if (q + 1 < nd) {
+        const double2 a = *reinterpret_cast<const double2 *>(x + d0 + q);
+        const double2 b = *reinterpret_cast<const double2 *>(v + d0 + q);
+        bx[q] = a.x;
+        bx[q + 1] = a.y;
+        bv[q] = b.x;
+        bv[q + 1] = b.y;
+      } else if (q < nd) {
+        bx[q] = x[d0 + q];
+        bv[q] = v[d0 + q];
+      }
+    }
+    __syncwarp();
+  }
+  for (int h = 0; h < 2; ++h) {
+    const int l = 32 * h + lane;
+    const long long row = r0 + l;
+    if (row < rows) {
+      const int k = find_inst(offs, n, row);
+      const Inst &I = insts[k];
+      const int i = (int)(row - offs[k]);
+      for (int c = 0; c < 3; ++c) {
+        if (unpack) {
+          I.x[c * I.nv + i] = bx[3 * l + c];
+          I.v[c * I.nv + i] = bv[3 * l + c];
+        } else {
+          bx[3 * l + c] = I.x[c * I.nv + i];
+          bv[3 * l + c] = I.v[c * I.nv + i];
+        }
+      }
+    }
+  }
+  if (!unpack) {
+    __syncwarp();
+    for (int j = 0; j < 3; ++j) {
+      const int q = 2 * (32 * j + lane);
+      if (q + 1 < nd) {
+        *reinterpret_cast<double2 *>(x + d0 + q) = make_double2(bx[q], bx[q + 1]);
+        *reinterpret_cast<double2 *>(v + d0 + q) = make_double2(bv[q], bv[q + 1]);
+      } else if (q < nd) {
+        x[d0 + q] = bx[q];
+        v[d0 + q] = bv[q];
+      }
     }
   }
 }
@@ -183,7 +251,13 @@ cudaError_t launch_matvec64(const Inst *d, const Inst &h, const double *in, doub
 cudaError_t launch_pack_states(const Inst *d_insts, int n, const long long *d_offs, long long rows, double *d_x,
                                double *d_v, int unpack, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  k_pack_states<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(d_insts, n, d_offs, d_x, d_v, unpack);
+  if ((reinterpret_cast<uintptr_t>(d_x) | reinterpret_cast<uintptr_t>(d_v)) % 16 == 0) {
+    const long long per_block = 8LL * kPackRowsPerWarp;
+    k_pack_states_vec<<<(unsigned)((rows + per_block - 1) / per_block), 256, 0, st>>>(d_insts, n, d_offs, d_x, d_v,
+                                                                                    unpack);
+  } else {
+    k_pack_states<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(d_insts, n, d_offs, d_x, d_v, unpack);
+  }
   return cudaGetLastError();
 }
 

@@ -343,6 +343,43 @@ def test_batch_step_states_equals_set_step_get():
     assert runs[0][4] == runs[1][4]
 
 
+def test_batch_states_from_page_locked_buffers():
+    """Page-locked host buffers are read and written in place by the state kernels (no staging copy); the
+    states, statistics and every later step equal those of pageable buffers (staged copies), bitwise: set,
+    step and get in one call, in separate calls, and in place (the same buffers in and out)."""
+    import torch
+    scs = sg.mixed_batch(6, seed=36, side_lo=4, side_hi=40)
+    runs = []
+    for pinned in (False, True):
+        b = gb.shell_batch_create(1 << 40)
+        hs = [gb.create_from_scenario(sc, precision="fp32_refine") for sc in scs]
+        for h in hs:
+            gb.shell_batch_admit(b, h)
+        gb.shell_batch_step(b, 2)
+        x0, v0 = gb.shell_batch_get_states(b)
+
+        def buf(a):
+            if not pinned:
+                return np.array(a)
+            t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True).numpy()
+            t[...] = a
+            return t
+        x, v = buf(x0 * 1.0001), buf(v0 * 0.5)
+        xo, vo = buf(np.zeros_like(x0)), buf(np.zeros_like(v0))
+        rc, st = gb.shell_batch_step_states(b, 3, x, v, xo, vo)
+        gb.shell_batch_set_states(b, xo, vo)
+        rc2, _ = gb.shell_batch_step(b, 1)
+        gb.shell_batch_get_states(b, x, v)
+        rc3, _ = gb.shell_batch_step_states(b, 2, x, v, x, v)        # in place
+        assert rc == 0 and rc2 == 0 and rc3 == 0
+        runs.append((np.array(xo), np.array(vo), np.array(x), np.array(v),
+                     {k: (s["steps_done"], s["total_pcg_iterations"]) for k, s in st.items()}))
+        gb.shell_batch_destroy(b)
+    for a, c in zip(runs[0][:4], runs[1][:4]):
+        assert np.array_equal(a, c)
+    assert runs[0][4] == runs[1][4]
+
+
 @pytest.mark.parametrize("case", ["cyl96_SS", "jitter160_SP", "batch6"])
 def test_shared_memory_staging_is_bitwise_neutral(case):
     """FP32 products that stage each 256-row block's gathered vector entries in shared memory read the same
