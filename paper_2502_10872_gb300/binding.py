@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+from collections.abc import Mapping
 from typing import Optional
 
 import numpy as np
@@ -429,6 +430,47 @@ class Batch:
         self.ptr = ptr
         self._opts = opts
         self.members = {}
+        self._layout = None    # (slots, row offsets) of the packed state layout, until the next admit / retire
+        self._slots = None     # resident slots in increasing order, likewise
+
+    def _changed(self):
+        self._layout = None
+        self._slots = None
+
+    def resident_slots(self) -> tuple:
+        if self._slots is None:
+            self._slots = tuple(sorted(self.members))
+        return self._slots
+
+
+class BatchStats(Mapping):
+    """Statistics of one batch call: slot -> dict of the shell_step_stats fields, for the resident slots.
+    Each slot's dict is built when first read, so a call whose statistics are not read pays nothing for
+    them."""
+    __slots__ = ("_arr", "_keys", "_cache")
+
+    def __init__(self, arr, keys):
+        self._arr = arr
+        self._keys = keys
+        self._cache = {}
+
+    def __getitem__(self, slot):
+        d = self._cache.get(slot)
+        if d is None:
+            if slot not in self._keys:
+                raise KeyError(slot)
+            d = self._cache[slot] = self._arr[slot].as_dict()
+        return d
+
+    def raw(self, slot):
+        """The slot's shell_step_stats record itself (fields as attributes), or None if not resident."""
+        return self._arr[slot] if slot in self._keys else None
+
+    def __iter__(self):
+        return iter(self._keys)
+
+    def __len__(self):
+        return len(self._keys)
 
     def __del__(self):
         if getattr(self, "ptr", None):
@@ -454,22 +496,25 @@ def shell_batch_admit(b: Batch, h: Handle, check: bool = True) -> int:
     elif rc != SHELL_OK:
         return rc
     b.members[slot.value] = h
+    b._changed()
     return slot.value
 
 
 def shell_batch_retire(b: Batch, slot: int):
     _check(load_library().shell_batch_retire(b.ptr, int(slot)), "shell_batch_retire")
     b.members.pop(slot, None)
+    b._changed()
 
 
 def shell_batch_step(b: Batch, n_steps: int = 1, check: bool = True):
+    """Step every resident instance n_steps times: (rc, BatchStats: slot -> statistics of the call)."""
     lib = load_library()
     cap = lib.shell_batch_capacity(b.ptr)
     stats = (shell_step_stats * max(1, cap))()
     rc = lib.shell_batch_step(b.ptr, int(n_steps), stats)
     if check:
         _check(rc, "shell_batch_step")
-    return rc, {k: stats[k].as_dict() for k in range(cap) if k in b.members}
+    return rc, BatchStats(stats, b.resident_slots())
 
 
 def shell_batch_step_times(b: Batch, n: int) -> np.ndarray:
@@ -512,13 +557,19 @@ def shell_batch_set_launch(b: Batch, ctas_per_sm: int, share_scale: float = 1.0,
 
 
 def shell_batch_state_layout(b: Batch):
-    """(slots, row_offsets) of the packed state layout: resident slots in increasing order."""
-    lib = load_library()
-    n = lib.shell_batch_state_layout(b.ptr, None, None)
-    slots = np.zeros(max(1, n), np.int32)
-    offs = np.zeros(n + 1, np.int64)
-    lib.shell_batch_state_layout(b.ptr, slots.ctypes.data, offs.ctypes.data)
-    return slots[:n], offs
+    """(slots, row_offsets) of the packed state layout: resident slots in increasing order (read once per
+    admit / retire; the arrays are read-only)."""
+    if b._layout is None:
+        lib = load_library()
+        n = lib.shell_batch_state_layout(b.ptr, None, None)
+        slots = np.zeros(max(1, n), np.int32)
+        offs = np.zeros(n + 1, np.int64)
+        lib.shell_batch_state_layout(b.ptr, slots.ctypes.data, offs.ctypes.data)
+        slots, offs = slots[:n], offs
+        slots.flags.writeable = False
+        offs.flags.writeable = False
+        b._layout = (slots, offs)
+    return b._layout
 
 
 def shell_batch_get_states(b: Batch, x_out=None, v_out=None):
@@ -555,7 +606,7 @@ def shell_batch_step_states(b: Batch, n_steps: int, x_in=None, v_in=None, x_out=
     rc = lib.shell_batch_step_states(b.ptr, int(n_steps), ptr(x_in), ptr(v_in), ptr(x_out), ptr(v_out), stats)
     if check:
         _check(rc, "shell_batch_step_states")
-    return rc, {k: stats[k].as_dict() for k in range(cap) if k in b.members}
+    return rc, BatchStats(stats, b.resident_slots())
 
 
 def shell_batch_destroy(b: Batch):
@@ -563,3 +614,4 @@ def shell_batch_destroy(b: Batch):
         _check(load_library().shell_batch_destroy(b.ptr), "shell_batch_destroy")
         b.ptr = None
         b.members.clear()
+        b._changed()

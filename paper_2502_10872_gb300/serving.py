@@ -154,13 +154,13 @@ class Server:
             lat.extend(gb.shell_batch_step_times(self.batch, n).tolist())
             nsteps += n
             for slot, req in list(active.items()):
-                st = stats.get(slot)
+                st = stats.raw(slot)
                 if st is None:
                     continue
-                req.done_steps += st["steps_done"]
-                vsteps += st["steps_done"] * req.scenario.n_verts
-                if st["status"] != 0:
-                    req.status = st["status"]
+                req.done_steps += st.steps_done
+                vsteps += st.steps_done * req.scenario.n_verts
+                if st.status != 0:
+                    req.status = st.status
                 if req.done_steps >= req.steps or req.status != 0:
                     req.finished_s = now()
                     if self.keep_states:

@@ -89,3 +89,31 @@ def test_binding_struct_offsets_match_the_c_compiler(tmp_path):
         assert int(got[name]) == C.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_batch_stats_mapping():
+    """The per-call batch statistics are a read-only mapping over the resident slots (ascending), each slot's
+    fields read from the C array when first accessed; slots outside the batch are absent."""
+    arr = (binding.shell_step_stats * 8)()
+    for k in range(8):
+        arr[k].steps_done = k
+        arr[k].total_pcg_iterations = 10 * k
+    st = binding.BatchStats(arr, (1, 4, 6))
+    assert list(st) == [1, 4, 6] and len(st) == 3
+    assert st[4]["steps_done"] == 4 and st[6]["total_pcg_iterations"] == 60
+    assert 2 not in st and st.get(2) is None
+    with pytest.raises(KeyError):
+        st[0]
+    assert [s["steps_done"] for s in st.values()] == [1, 4, 6]
+    assert dict(st.items())[1]["status"] == 0
+    assert st[4] is st[4]   # built once
+    assert st.raw(6).total_pcg_iterations == 60 and st.raw(2) is None
+
+
+def test_batch_resident_slots_follow_membership():
+    b = binding.Batch(None, None)
+    b.members = {5: None, 2: None}
+    assert b.resident_slots() == (2, 5)
+    b.members[0] = None
+    b._changed()
+    assert b.resident_slots() == (0, 2, 5)
