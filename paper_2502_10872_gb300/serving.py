@@ -73,9 +73,17 @@ class ServeReport:
 class Server:
     """Admit requests into one batch by an HBM budget and step them together."""
 
+    # Launch shape of the batch's step kernel (CTAs per SM, CTA-share scale, clusters), measured on the
+    # serving mix (1k-250k-vertex requests): the 5-CTA-per-SM variant with a small share scale, so that the
+    # largest resident requests get large teams. Serving, 10 s on one box: the library's default (3 CTAs per
+    # SM, share 1) 134.8 M vertex-steps/s; (5, 2.0), the shape the autotuner picks for batches of instances
+    # of at most 66 row blocks, 51.8-56.3 M; (5, 1.0) 131.1 M; (5, 0.5) 186.3 M; (5, 0.25) 203.7-205.4 M;
+    # (5, 0.125) 211.6 M; (5, 0.0625) 208.8 M. None keeps the library's default.
+    DEFAULT_LAUNCH = (5, 0.125, False)
+
     def __init__(self, budget_bytes: int, precision: str = "fp32_refine", keep_states: bool = False,
                  create_kw: Optional[dict] = None, clock: Callable[[], float] = time.perf_counter,
-                 n_workers: int = 4):
+                 n_workers: int = 4, launch: Optional[tuple] = DEFAULT_LAUNCH):
         self.budget = int(budget_bytes)
         self.n_workers = max(1, int(n_workers))
         self.device = None
@@ -90,6 +98,8 @@ class Server:
         self.create_kw = create_kw or {}
         self.clock = clock
         self.batch = gb.shell_batch_create(self.budget)
+        if launch is not None:
+            gb.shell_batch_set_launch(self.batch, *launch)
         self.used = 0
 
     def _create(self, req: Request):
