@@ -17,10 +17,73 @@
 
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 namespace shl {
 
 namespace {
+
+// Host threads for the row-parallel parts of the set-up (sparse products, the smoothed prolongation, the
+// power iteration): up to 4, and only for matrices large enough to repay starting them.
+int setup_threads(int n) {
+  if (n < 16384) return 1;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(4u, hw));
+}
+
+// Runs fn(t, lo, hi) for the T contiguous chunks [lo, hi) of [0, n), chunk 0 on the calling thread.
+template <typename F>
+void parallel_chunks(int n, int T, F &&fn) {
+  auto run = [&](int t) { fn(t, (int)((long long)n * t / T), (int)((long long)n * (t + 1) / T)); };
+  if (T <= 1) {
+    run(0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
+  run(0);
+  for (std::thread &x : th) x.join();
+}
+
+// Per-thread scratch of a row computation: a dense marker and accumulator over the columns, the row's columns.
+struct RowWork {
+  std::vector<int32_t> mark;
+  std::vector<double> acc;
+  std::vector<int32_t> cols;
+};
+
+// CSR matrix of n rows and m columns whose row i row_fn(i, work, cols, vals) appends. Rows are computed by
+// contiguous chunks on setup_threads(n) threads, each row exactly as a serial loop computes it, so the
+// matrix does not depend on the number of threads.
+template <typename F>
+HostCsr build_rows(int n, int m, F &&row_fn) {
+  const int T = setup_threads(n);
+  std::vector<std::vector<int32_t>> cols(T);
+  std::vector<std::vector<double>> vals(T);
+  std::vector<int32_t> len(n);
+  parallel_chunks(n, T, [&](int t, int lo, int hi) {
+    RowWork w;
+    w.mark.assign(m, -1);
+    w.acc.assign(m, 0.0);
+    for (int i = lo; i < hi; ++i) {
+      const size_t before = cols[t].size();
+      row_fn(i, w, cols[t], vals[t]);
+      len[i] = (int32_t)(cols[t].size() - before);
+    }
+  });
+  HostCsr C;
+  C.n = n;
+  C.m = m;
+  C.ptr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) C.ptr[i + 1] = C.ptr[i] + len[i];
+  C.col.reserve(C.ptr[n]);
+  C.val.reserve(C.ptr[n]);
+  for (int t = 0; t < T; ++t) {
+    C.col.insert(C.col.end(), cols[t].begin(), cols[t].end());
+    C.val.insert(C.val.end(), vals[t].begin(), vals[t].end());
+  }
+  return C;
+}
 
 HostCsr transpose(const HostCsr &M) {
   HostCsr T;
@@ -43,36 +106,27 @@ HostCsr transpose(const HostCsr &M) {
 
 // C = A * B (sparse, rows accumulated with a dense marker)
 HostCsr multiply(const HostCsr &A, const HostCsr &B) {
-  HostCsr C;
-  C.n = A.n;
-  C.m = B.m;
-  C.ptr.assign(C.n + 1, 0);
-  std::vector<int32_t> mark(B.m, -1);
-  std::vector<double> acc(B.m, 0.0);
-  std::vector<int32_t> cols;
-  for (int i = 0; i < A.n; ++i) {
-    cols.clear();
+  return build_rows(A.n, B.m, [&](int i, RowWork &w, std::vector<int32_t> &oc, std::vector<double> &ov) {
+    w.cols.clear();
     for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) {
       const int k = A.col[q];
       const double a = A.val[q];
       for (int r = B.ptr[k]; r < B.ptr[k + 1]; ++r) {
         const int j = B.col[r];
-        if (mark[j] != i) {
-          mark[j] = i;
-          acc[j] = 0.0;
-          cols.push_back(j);
+        if (w.mark[j] != i) {
+          w.mark[j] = i;
+          w.acc[j] = 0.0;
+          w.cols.push_back(j);
         }
-        acc[j] += a * B.val[r];
+        w.acc[j] += a * B.val[r];
       }
     }
-    std::sort(cols.begin(), cols.end());
-    for (int j : cols) {
-      C.col.push_back(j);
-      C.val.push_back(acc[j]);
+    std::sort(w.cols.begin(), w.cols.end());
+    for (int j : w.cols) {
+      oc.push_back(j);
+      ov.push_back(w.acc[j]);
     }
-    C.ptr[i + 1] = (int32_t)C.col.size();
-  }
-  return C;
+  });
 }
 
 double diag_of(const HostCsr &A, int i) {
@@ -87,14 +141,17 @@ double rho_dinv_a(const HostCsr &A, const std::vector<double> &dinv) {
   std::vector<double> x(n), y(n);
   for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * std::sin(1.7 * i + 0.3);
   double lam = 1.0;
+  const int T = setup_threads(n);
   for (int it = 0; it < 20; ++it) {
-    double nrm = 0.0;
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
-      y[i] = dinv[i] * s;
-      nrm += y[i] * y[i];
-    }
+    parallel_chunks(n, T, [&](int, int lo, int hi) {
+      for (int i = lo; i < hi; ++i) {
+        double s = 0.0;
+        for (int q = A.ptr[i]; q < A.ptr[i + 1]; ++q) s += A.val[q] * x[A.col[q]];
+        y[i] = dinv[i] * s;
+      }
+    });
+    double nrm = 0.0;   // summed in row order, as the rows were before
+    for (int i = 0; i < n; ++i) nrm += y[i] * y[i];
     nrm = std::sqrt(nrm);
     double xn = 0.0;
     for (int i = 0; i < n; ++i) xn += x[i] * x[i];
@@ -276,22 +333,15 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
     const int na = aggregate(F.A, theta, agg);
     if (na == 0 || na > (int)(0.8 * n)) break;   // coarsening stalled
     // P = (I - omega D^-1 A) P0
-    HostCsr P;
-    P.n = n;
-    P.m = na;
-    P.ptr.assign(n + 1, 0);
-    std::vector<int32_t> mark(na, -1);
-    std::vector<double> acc(na, 0.0);
-    std::vector<int32_t> cols;
-    for (int i = 0; i < n; ++i) {
-      cols.clear();
+    const HostCsr P = build_rows(n, na, [&](int i, RowWork &w, std::vector<int32_t> &oc, std::vector<double> &ov) {
+      w.cols.clear();
       auto add = [&](int c, double v) {
-        if (mark[c] != i) {
-          mark[c] = i;
-          acc[c] = 0.0;
-          cols.push_back(c);
+        if (w.mark[c] != i) {
+          w.mark[c] = i;
+          w.acc[c] = 0.0;
+          w.cols.push_back(c);
         }
-        acc[c] += v;
+        w.acc[c] += v;
       };
       if (agg[i] >= 0) add(agg[i], 1.0);
       if (agg[i] != -1) {   // rows left out (isolated) get no prolongation
@@ -300,42 +350,37 @@ void build_amg(const HostCsr &A0, HostAmg *out, int max_levels, int coarse_max, 
           if (agg[j] >= 0) add(agg[j], -F.omega * F.dinv[i] * F.A.val[q]);
         }
       }
-      std::sort(cols.begin(), cols.end());
-      for (int c : cols)
-        if (acc[c] != 0.0) {
-          P.col.push_back(c);
-          P.val.push_back(acc[c]);
+      std::sort(w.cols.begin(), w.cols.end());
+      for (int c : w.cols)
+        if (w.acc[c] != 0.0) {
+          oc.push_back(c);
+          ov.push_back(w.acc[c]);
         }
-      P.ptr[i + 1] = (int32_t)P.col.size();
-    }
+    });
     F.P = P;
     F.R = transpose(P);
     const HostCsr AP = multiply(F.A, P);
     // Ps = P - omega D^-1 (A P), merged row by row (both rows sorted by column), and Rs = Ps^T
-    HostCsr &Ps = F.Ps;
-    Ps.n = n;
-    Ps.m = na;
-    Ps.ptr.assign(n + 1, 0);
-    for (int i = 0; i < n; ++i) {
+    F.Ps = build_rows(n, na, [&](int i, RowWork &, std::vector<int32_t> &oc, std::vector<double> &ov) {
       int q = P.ptr[i];
       const int q1 = P.ptr[i + 1];
       const double s = -F.omega * F.dinv[i];
       for (int k = AP.ptr[i]; k < AP.ptr[i + 1]; ++k) {
         for (; q < q1 && P.col[q] < AP.col[k]; ++q) {
-          Ps.col.push_back(P.col[q]);
-          Ps.val.push_back(P.val[q]);
+          oc.push_back(P.col[q]);
+          ov.push_back(P.val[q]);
         }
         double v = s * AP.val[k];
         if (q < q1 && P.col[q] == AP.col[k]) v += P.val[q++];
-        Ps.col.push_back(AP.col[k]);
-        Ps.val.push_back(v);
+        oc.push_back(AP.col[k]);
+        ov.push_back(v);
       }
       for (; q < q1; ++q) {
-        Ps.col.push_back(P.col[q]);
-        Ps.val.push_back(P.val[q]);
+        oc.push_back(P.col[q]);
+        ov.push_back(P.val[q]);
       }
-      Ps.ptr[i + 1] = (int32_t)Ps.col.size();
-    }
+    });
+    const HostCsr &Ps = F.Ps;
     F.Rs = transpose(Ps);
     HostCsr Ac = multiply(F.R, AP);
     H.levels.emplace_back();

@@ -41,6 +41,7 @@ def scenes():
     yield "plate EP 40", sg.plate_clamped_x0(40, model="EP")
     yield "cylinder SS 32", sg.cylinder_panel(32, "SS")
     yield "jittered SP 48", sg.jittered_plate(48, steps=1)
+    yield "plate FP 130", sg.plate_clamped_x0(130, model="FP")   # 17,161 rows: the threaded set-up path
     for k, sc in enumerate(sg.mixed_batch(3, seed=9, side_lo=20, side_hi=40)):
         yield f"mixed {k} {sc.model}", sc
 
