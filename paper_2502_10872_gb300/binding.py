@@ -431,7 +431,7 @@ class Batch:
         self._opts = opts
         self.members = {}
         self._layout = None    # (slots, row offsets) of the packed state layout, until the next admit / retire
-        self._slots = None     # resident slots in increasing order, likewise
+        self._slots = None     # resident slots in increasing order and as a set, likewise
 
     def _changed(self):
         self._layout = None
@@ -439,7 +439,12 @@ class Batch:
 
     def resident_slots(self) -> tuple:
         if self._slots is None:
-            self._slots = tuple(sorted(self.members))
+            keys = tuple(sorted(self.members))
+            self._slots = (keys, frozenset(keys))
+        return self._slots[0]
+
+    def _resident(self):
+        self.resident_slots()
         return self._slots
 
 
@@ -447,24 +452,28 @@ class BatchStats(Mapping):
     """Statistics of one batch call: slot -> dict of the shell_step_stats fields, for the resident slots.
     Each slot's dict is built when first read, so a call whose statistics are not read pays nothing for
     them."""
-    __slots__ = ("_arr", "_keys", "_cache")
+    __slots__ = ("_arr", "_keys", "_set", "_cache")
 
-    def __init__(self, arr, keys):
+    def __init__(self, arr, keys, key_set=None):
         self._arr = arr
-        self._keys = keys
+        self._keys = tuple(keys)
+        self._set = frozenset(self._keys) if key_set is None else key_set
         self._cache = {}
 
     def __getitem__(self, slot):
         d = self._cache.get(slot)
         if d is None:
-            if slot not in self._keys:
+            if slot not in self._set:
                 raise KeyError(slot)
             d = self._cache[slot] = self._arr[slot].as_dict()
         return d
 
+    def __contains__(self, slot):
+        return slot in self._set
+
     def raw(self, slot):
         """The slot's shell_step_stats record itself (fields as attributes), or None if not resident."""
-        return self._arr[slot] if slot in self._keys else None
+        return self._arr[slot] if slot in self._set else None
 
     def __iter__(self):
         return iter(self._keys)
@@ -514,7 +523,7 @@ def shell_batch_step(b: Batch, n_steps: int = 1, check: bool = True):
     rc = lib.shell_batch_step(b.ptr, int(n_steps), stats)
     if check:
         _check(rc, "shell_batch_step")
-    return rc, BatchStats(stats, b.resident_slots())
+    return rc, BatchStats(stats, *b._resident())
 
 
 def shell_batch_step_times(b: Batch, n: int) -> np.ndarray:
@@ -606,7 +615,7 @@ def shell_batch_step_states(b: Batch, n_steps: int, x_in=None, v_in=None, x_out=
     rc = lib.shell_batch_step_states(b.ptr, int(n_steps), ptr(x_in), ptr(v_in), ptr(x_out), ptr(v_out), stats)
     if check:
         _check(rc, "shell_batch_step_states")
-    return rc, BatchStats(stats, b.resident_slots())
+    return rc, BatchStats(stats, *b._resident())
 
 
 def shell_batch_destroy(b: Batch):
