@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <system_error>
 #include <thread>
 
 namespace shl {
@@ -31,7 +32,9 @@ int setup_threads(int n) {
   return (int)std::max(1u, std::min(4u, hw));
 }
 
-// Runs fn(t, lo, hi) for the T contiguous chunks [lo, hi) of [0, n), chunk 0 on the calling thread.
+// Runs fn(t, lo, hi) for the T contiguous chunks [lo, hi) of [0, n), chunk 0 on the calling thread. A chunk
+// whose thread cannot be started runs on the calling thread instead (each chunk writes only its own outputs,
+// so the result is the same).
 template <typename F>
 void parallel_chunks(int n, int T, F &&fn) {
   auto run = [&](int t) { fn(t, (int)((long long)n * t / T), (int)((long long)n * (t + 1) / T)); };
@@ -40,8 +43,13 @@ void parallel_chunks(int n, int T, F &&fn) {
     return;
   }
   std::vector<std::thread> th;
-  for (int t = 1; t < T; ++t) th.emplace_back(run, t);
+  int started = 1;
+  try {
+    for (; started < T; ++started) th.emplace_back(run, started);
+  } catch (const std::system_error &) {
+  }
   run(0);
+  for (int t = started; t < T; ++t) run(t);
   for (std::thread &x : th) x.join();
 }
 
