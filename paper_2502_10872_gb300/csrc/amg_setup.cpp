@@ -25,11 +25,14 @@ namespace shl {
 namespace {
 
 // Host threads for the row-parallel parts of the set-up (sparse products, the smoothed prolongation, the
-// power iteration): up to 4, and only for matrices large enough to repay starting them.
+// power iteration): up to setup_threads_cap, and only for matrices of at least setup_threads_min_rows rows,
+// large enough to repay starting them. (Variables, so that the host check can compare thread counts.)
+int setup_threads_cap = 4;
+int setup_threads_min_rows = 16384;
 int setup_threads(int n) {
-  if (n < 16384) return 1;
+  if (n < setup_threads_min_rows) return 1;
   const unsigned hw = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(4u, hw));
+  return (int)std::max(1u, std::min((unsigned)std::max(1, setup_threads_cap), hw));
 }
 
 // Runs fn(t, lo, hi) for the T contiguous chunks [lo, hi) of [0, n), chunk 0 on the calling thread. A chunk

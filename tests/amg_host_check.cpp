@@ -1,6 +1,7 @@
 // Host check of the multigrid set-up used by the solve kernel (built and run by test_host_multigrid.py; no
 // GPU). Reads a scalar CSR matrix (int32 n, nnz; int32 ptr[n+1], col[nnz]; double val[nnz]), builds the
-// hierarchy with the library's own set-up code, and checks on every level with a next one:
+// hierarchy with the library's own set-up code, checks that the hierarchy is bitwise the same when its
+// row-parallel parts run on 1 or 3 threads, and checks on every level with a next one:
 //   1. Ps is exactly Rs^T (structure and values);
 //   2. Rs equals R (I - omega A D^-1) formed by an explicit sparse product;
 // and, for three right-hand sides, that the cycle the kernel runs (per level one down step r = b - A x,
@@ -65,6 +66,37 @@ int main(int argc, char **argv) {
   if (got != (size_t)A.n + 1 + 2 * (size_t)hdr[1]) return 2;
   HostAmg H;
   build_amg(A, &H);
+  // the same hierarchy, bit for bit, whatever the number of set-up threads (the row-parallel parts are
+  // forced onto 1 and onto 3 threads, for any matrix size)
+  {
+    const int cap = setup_threads_cap, min_rows = setup_threads_min_rows;
+    setup_threads_min_rows = 1;
+    HostAmg H1, H3;
+    setup_threads_cap = 1;
+    build_amg(A, &H1);
+    setup_threads_cap = 3;
+    build_amg(A, &H3);
+    setup_threads_cap = cap;
+    setup_threads_min_rows = min_rows;
+    auto same_csr = [](const HostCsr &a, const HostCsr &b) {
+      return a.n == b.n && a.m == b.m && a.ptr == b.ptr && a.col == b.col && a.val == b.val;
+    };
+    const HostAmg *hs[3] = {&H, &H1, &H3};
+    for (int k = 1; k < 3; ++k) {
+      const HostAmg &X = *hs[k];
+      bool same = X.levels.size() == H.levels.size() && X.coarse_inv == H.coarse_inv &&
+                  X.coarse_sweeps == H.coarse_sweeps && X.dense_level == H.dense_level && X.dense == H.dense;
+      for (size_t l = 0; same && l < H.levels.size(); ++l) {
+        const HostAmgLevel &a = H.levels[l], &b = X.levels[l];
+        same = same_csr(a.A, b.A) && same_csr(a.P, b.P) && same_csr(a.R, b.R) && same_csr(a.Rs, b.Rs) &&
+               same_csr(a.Ps, b.Ps) && a.dinv == b.dinv && a.rowsum == b.rowsum && a.omega == b.omega;
+      }
+      if (!same) {
+        printf("FAIL the hierarchy depends on the number of set-up threads (%d)\n", k == 1 ? 1 : 3);
+        return 1;
+      }
+    }
+  }
   const int L = (int)H.levels.size();
   if (L < 2) {
     printf("FAIL no hierarchy (%d level)\n", L);
