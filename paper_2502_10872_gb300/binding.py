@@ -447,6 +447,14 @@ class Batch:
         self.resident_slots()
         return self._slots
 
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                load_library().shell_batch_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
 
 class BatchStats(Mapping):
     """Statistics of one batch call: slot -> dict of the shell_step_stats fields, for the resident slots.
@@ -480,14 +488,6 @@ class BatchStats(Mapping):
 
     def __len__(self):
         return len(self._keys)
-
-    def __del__(self):
-        if getattr(self, "ptr", None):
-            try:
-                load_library().shell_batch_destroy(self.ptr)
-            except Exception:
-                pass
-            self.ptr = None
 
 
 def shell_batch_create(budget_bytes: int, stream=None, use_torch_allocator=True) -> Batch:

@@ -111,6 +111,7 @@ def test_batch_stats_mapping():
 
 
 def test_batch_resident_slots_follow_membership():
+    assert "__del__" in binding.Batch.__dict__   # a collected batch frees its device memory
     b = binding.Batch(None, None)
     b.members = {5: None, 2: None}
     assert b.resident_slots() == (2, 5)
